@@ -1,0 +1,289 @@
+"""Benchmark: eigenpairs/s of POLFED on synthetic disordered chains (one GB300 per rank).
+
+A step is one whole polfed_eigs run (spectral bounds, K from the density of
+states, block Lanczos on the Chebyshev filter with full re-orthogonalization,
+Ritz vectors, Rayleigh-Ritz with H~, residual check) on one disorder
+realization.  Ranks (torchrun) run independent realizations (weak scaling, no
+data-path collective).  Prints one JSON line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import polfed_inputs as I  # noqa: E402
+
+METRIC = "eigenpairs/s at L=22, ε=0.5 (resid≤1e-8‖H‖); filter GB/s vs HBM peak"
+WORKLOADS = {
+    # name: (builder, L, W, N_ev, n_b, config id of the field generator)
+    "L22_xxz_W3": (I.xxz, 22, 3.0, 500, 64, 4),
+    "L20_j1j2_W4": (I.j1j2, 20, 4.0, 200, 32, 2),
+    "L14_xxz_W3": (I.xxz, 14, 3.0, 50, 16, 1),
+    "L24_j1j2_W5": (I.j1j2, 24, 5.0, 1000, 64, 5),
+}
+PREC = {"df64": 2, "f64": 0, "f32": 1}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def step_kernel_traffic():
+    """DRAM bytes per step-kernel launch from the committed ncu summary, if it
+    was taken on the current kernel source (else None)."""
+    src = os.path.join(ROOT, "paper_2005_09534_gb300", "csrc", "hamiltonian.cu")
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        with open(os.path.join(ROOT, "profiles", "step_kernel_traffic.json")) as f:
+            d = json.load(f)
+        if d.get("source_sha") == sha:
+            return d
+    except Exception:
+        pass
+    return None
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except Exception:
+            self.p.kill()
+            out = ""
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_sample(seconds=12.0):
+    """The CPU oracle (dense ED of the S^z=0 block, LAPACK eigh) on L=14 XXZ chains,
+    N_ev=50 nearest eps=0.5, repeated over realizations for about `seconds`."""
+    import oracle as O
+    t0 = time.perf_counter()
+    n_pairs, n_real = 0, 0
+    while True:
+        m = I.xxz(14, 3.0, 1, 100 + n_real)
+        r = O.eigs_nearest(m.L, m.J1, m.J2, m.Delta, m.h, True, 0.5, 50)
+        n_pairs += len(r["evals"])
+        n_real += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": n_pairs / dt, "unit": "eigenpairs/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"dense ED (numpy eigh, default BLAS threads) of {n_real} L=14 XXZ W=3 realizations, "
+                      f"N_ev=50 each, {dt:.1f} s; dense ED at L=22 (705432^2 FP64, 4 TB) is infeasible"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_sample(0.0)
+    vals = []
+    t_all = 0.0
+    for _ in range(args.steps):
+        s = oracle_sample(3.0)
+        vals.append(s["value"])
+        t_all += 50.0 / s["value"]
+    value = float(np.mean(vals))
+    cb = oracle_sample(3.0)
+    cb["value"] = value
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "eigenpairs/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * 50.0 / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "L14_xxz_W3 dense-ED sample (bounded stand-in for " + args.workload + ")",
+                       "N_ev": 50, "eps": 0.5},
+            "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": "eigenpairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="L22_xxz_W3", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="df64", choices=sorted(PREC))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        print("warning: fewer than 3 warm-up steps; the number is not valid", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2005_09534_gb300 as pf
+
+    builder, L, W, n_ev, n_b, cfg = WORKLOADS[args.workload]
+    dim = pf.basis_build(L, L // 2)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = pf.Ctx(local)
+    ctx.set_stream(stream)
+    opts = pf.opts_default()
+    opts.precision = PREC[args.precision]
+    evecs = torch.empty((n_ev, dim), dtype=torch.float64, device=dev)  # column-major dim x N_ev
+    host_evecs = torch.empty((n_ev, dim), dtype=torch.float64, pin_memory=True)
+    fields_pinned = torch.empty(L, dtype=torch.float64, pin_memory=True)
+
+    def one(realization, copy_out):
+        m = builder(L, W, cfg, realization)
+        fields_pinned.copy_(torch.from_numpy(m.h))
+        model = pf.Model(L, m.J1, m.J2, m.Delta, fields_pinned.numpy(), m.periodic)
+        ev, res, st, rc = pf.eigs(ctx, model, 0.5, n_ev, 0, n_b, opts, d_evecs=evecs, allow_noconv=True)
+        hn = max(abs(st["E_min"]), abs(st["E_max"]))
+        ok = int(np.sum(res[: len(ev)] <= 1e-8 * hn)) if rc == 0 else 0
+        return ok, st, rc, float(np.max(res) / hn)
+
+    for w in range(args.warmup):
+        one(10_000 + w * world + rank, False)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = Clocks(local)
+    if rank == 0:
+        clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    dev_ms, wall_s, pairs = 0.0, 0.0, 0
+    agg = {"n_launches": 0, "n_step_launches": 0, "step_gpu_s": 0.0, "step_alg_bytes": 0.0, "K": [], "m": [],
+           "max_rel_resid": 0.0, "status": []}
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        e0.record(stream)
+        ok, st, rc, rr = one(k * world + rank, True)
+        e1.record(stream)
+        with torch.cuda.stream(stream):
+            host_evecs.copy_(evecs, non_blocking=True)
+        stream.synchronize()
+        wall_s += time.perf_counter() - t0
+        dev_ms += e0.elapsed_time(e1)
+        pairs += ok
+        for key in ("n_launches", "n_step_launches", "step_gpu_s", "step_alg_bytes"):
+            agg[key] += st[key]
+        agg["K"].append(st["K"])
+        agg["m"].append(st["m"])
+        agg["status"].append(rc)
+        agg["max_rel_resid"] = max(agg["max_rel_resid"], rr)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ck = clocks.stop() if rank == 0 else None
+    t_dev = dev_ms / 1e3
+    if dist:
+        tt = torch.tensor([t_dev, wall_s], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        pp = torch.tensor([pairs], device=dev, dtype=torch.float64)
+        dist.all_reduce(pp)
+        t_dev, wall_s = float(tt[0]), float(tt[1])
+        pairs_all = int(pp.item())
+    else:
+        pairs_all = pairs
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    peak, peak_kind = peaks()
+    avg_launch = agg["step_gpu_s"] / max(1, agg["n_step_launches"])
+    alg_per_launch = agg["step_alg_bytes"] / max(1, agg["n_step_launches"])
+    achieved = alg_per_launch / avg_launch / 1e9 if avg_launch > 0 else 0.0
+    tr = step_kernel_traffic()
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": (tr or {}).get("dram_bytes_per_launch"),
+            "peak_kind": f"of {peak_kind}", "kernel": "k_ham_step (Clenshaw step on a 128-byte column slice)",
+            "alg_bytes_per_launch": alg_per_launch, "avg_launch_us": round(avg_launch * 1e6, 2)}
+    value = pairs_all / t_dev
+    bytes_d2h = n_ev * dim * 8 + 2 * n_ev * 8
+    line = {"metric": METRIC, "value": round(value, 4), "unit": "eigenpairs/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * t_dev / args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
+            "data": "synthetic",
+            "config": {"workload": args.workload, "L": L, "dim": dim, "hamiltonian": builder.__name__,
+                       "W": W, "N_ev": n_ev, "n_b": n_b, "eps": 0.5, "K": agg["K"], "m": agg["m"],
+                       "parallelism": f"replicas x{world}", "l2": "per-step working set >> L2, no flush",
+                       "status": agg["status"], "max_resid_over_normH": agg["max_rel_resid"]},
+            "roofline": roof,
+            "e2e": {"value": round(pairs_all / wall_s, 4), "unit": "eigenpairs/s",
+                    "h2d_bytes_per_step": L * 8, "d2h_bytes_per_step": bytes_d2h},
+            "gpu_launches": int(agg["n_launches"]),
+            "clocks": ck}
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_sample()
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

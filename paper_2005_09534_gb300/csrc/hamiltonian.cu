@@ -1,0 +1,1137 @@
+// Matrix-free H~ application and the Clenshaw evaluation of P^K_sigma(H~) X.
+//
+// Eq. (1) in the S^z = 0 basis: the diagonal is sum_{bonds} J_l Delta z_i z_j
+// + sum_i h_i z_i (z = +-1/2) and every antiparallel pair (i, i+l) connects s
+// to s ^ (2^i | 2^(i+l)) with amplitude J_l / 2 (Supplement, "Technical
+// details": the off-diagonal elements are constants and are never loaded).
+// Rescaling (text before Eq. (3)): H~ = alpha (H - beta), alpha = 2/(e_hi - e_lo),
+// beta = (e_hi + e_lo)/2.
+//
+// Ranking.  Split a state into its low b bits s_lo and high L-b bits s_hi.
+// With the combinatorial number system, rank(s) = sum_k C(p_k, k+1) over the
+// set bits p_0 < p_1 < ...  The low bits contribute T_lo[s_lo] (the rank of
+// s_lo among b-bit strings of its popcount) and the high bits T_hi[s_hi]
+// (their indices are shifted by popc(s_lo) = L/2 - popc(s_hi)), so
+// rank(s) = T_hi[s_hi] + T_lo[s_lo].  All rows with one s_hi form a contiguous
+// "group" of C(b, L/2 - popc(s_hi)) rows starting at T_hi[s_hi].
+//
+// Kernel layout.  A CTA owns one group at a time and stages the group's rows
+// of the gather source b1 in shared memory.  A row's neighbours are then
+//   - low bonds (both sites in the low part): rows of the same group -> shared memory;
+//   - high bonds (both sites high): row T_hi[s_hi'] + local index, i.e. the
+//     same local row of another group -> coalesced global reads;
+//   - cross bonds (one site in each part): a gather inside a neighbour group.
+// Vectors are processed in column slices of 16*LPR bytes (LPR lanes per row,
+// 16 bytes per lane), stored slice-major (row stride = slice width).
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <type_traits>
+
+#include "polfed_internal.h"
+
+namespace polfed {
+
+// ------------------------------------------------------------- binomials
+__constant__ uint32_t c_binom[33][33];
+static uint32_t h_binom[33][33];
+static std::once_flag h_binom_once;
+
+static void init_binom() {
+  std::call_once(h_binom_once, [] {
+    memset(h_binom, 0, sizeof(h_binom));
+    for (int n = 0; n <= 32; n++) {
+      h_binom[n][0] = 1;
+      for (int k = 1; k <= n; k++) h_binom[n][k] = h_binom[n - 1][k - 1] + (k <= n - 1 ? h_binom[n - 1][k] : 0);
+    }
+  });
+}
+
+uint32_t binom_host(int n, int k) {
+  init_binom();
+  if (n < 0 || n > 32 || k < 0 || k > n) return 0;
+  return h_binom[n][k];
+}
+
+void upload_binomials() {
+  init_binom();
+  static std::mutex mu;
+  static uint64_t done = 0;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  if (dev < 64 && (done >> dev) & 1) return;
+  cudaMemcpyToSymbol(c_binom, h_binom, sizeof(h_binom));
+  if (dev < 64) done |= (1ull << dev);
+}
+
+// -------------------------------------------------------------- geometry
+static int choose_b(int L) {
+  // >= 2^10 groups at large L (load balance over 152 SMs) and a 128-byte-row
+  // group tile of C(11,5) * 128 B = 59 KB (three CTAs per SM)
+  int b = L - 10;
+  if (const char* e = getenv("POLFED_LOWBITS")) b = atoi(e);
+  if (b > 11) b = 11;
+  if (b < 2) b = 2;
+  if (L - b < 2) b = L - 2;
+  return b;
+}
+
+int build_geometry(const polfed_model* m, int b_override, HamGeometry* g) {
+  if (!m) return fail(POLFED_EINVAL, "model is NULL");
+  if (m->L < 4 || m->L > 32 || (m->L & 1)) return fail(POLFED_EINVAL, "L must be even, 4 <= L <= 32");
+  if (!m->h) return fail(POLFED_EINVAL, "model.h is NULL");
+  memset(g, 0, sizeof(*g));
+  const int L = m->L;
+  g->L = L;
+  g->n_up = L / 2;
+  g->periodic = m->periodic ? 1 : 0;
+  g->J1 = m->J1;
+  g->J2 = m->J2;
+  g->Delta = m->Delta;
+  for (int i = 0; i < L; i++) {
+    if (!std::isfinite(m->h[i])) return fail(POLFED_EINVAL, "non-finite field h_i");
+    g->h[i] = m->h[i];
+  }
+  if (!std::isfinite(m->J1) || !std::isfinite(m->J2) || !std::isfinite(m->Delta))
+    return fail(POLFED_EINVAL, "non-finite coupling");
+  g->dim = (int64_t)binom_host(L, L / 2);
+  int b = b_override > 0 ? b_override : choose_b(L);
+  if (b < 2 || L - b < 2) return fail(POLFED_EINVAL, "bad low/high split");
+  g->b = b;
+  g->nh = L - b;
+  // literal terms of Eq. (1): l = 1, 2 and i = 0..L-1 (j = i + l, wrapped if periodic)
+  std::vector<Bond> low, high, cross;
+  for (int l = 1; l <= 2; l++) {
+    double J = (l == 1) ? m->J1 : m->J2;
+    if (J == 0.0) continue;
+    for (int i = 0; i < L; i++) {
+      int j = i + l;
+      if (j >= L) {
+        if (!g->periodic) continue;
+        j -= L;
+      }
+      Bond bd{std::min(i, j), std::max(i, j), l};
+      if (bd.j < b)
+        low.push_back(bd);
+      else if (bd.i >= b)
+        high.push_back(bd);
+      else
+        cross.push_back(bd);
+    }
+  }
+  auto by_cls = [](const Bond& x, const Bond& y) { return x.cls < y.cls; };
+  std::stable_sort(low.begin(), low.end(), by_cls);
+  std::stable_sort(high.begin(), high.end(), by_cls);
+  if ((int)low.size() > kMaxBonds || (int)high.size() > kMaxBonds || (int)cross.size() > 8)
+    return fail(POLFED_EINVAL, "too many bonds for the table layout");
+  for (auto& x : low) {
+    g->low_mask[g->n_low1 + g->n_low2] = (1u << x.i) | (1u << x.j);
+    (x.cls == 1 ? g->n_low1 : g->n_low2)++;
+  }
+  for (auto& x : high) {
+    g->high_mask[g->n_high1 + g->n_high2] = (1u << (x.i - b)) | (1u << (x.j - b));
+    (x.cls == 1 ? g->n_high1 : g->n_high2)++;
+  }
+  for (auto& x : cross) {
+    g->cross_lo[g->n_cross] = x.i;
+    g->cross_hi[g->n_cross] = x.j - b;
+    g->cross_cls[g->n_cross] = x.cls;
+    g->n_cross++;
+  }
+  int off = 0;
+  for (int c = 0; c <= b + 1; c++) {
+    g->cls_off[c] = off;
+    if (c <= b) off += (int)binom_host(b, c);
+  }
+  {
+    const bool j2 = g->n_low2 + g->n_high2 > 0 || m->J2 != 0.0;
+    const int maxcr = j2 ? 6 : 2;
+    g->rec_stride = j2 ? 32 : 16;
+    if (1 + g->n_low1 + g->n_low2 + maxcr > g->rec_stride) return fail(POLFED_EINVAL, "too many low bonds for the record");
+  }
+  g->max_group = 0;
+  g->n_groups = 0;
+  for (int pc = 0; pc <= g->nh; pc++) {
+    int n_lo = g->n_up - pc;
+    if (n_lo < 0 || n_lo > b) continue;
+    g->max_group = std::max(g->max_group, (int)binom_host(b, n_lo));
+    g->n_groups += (int)binom_host(g->nh, pc);
+  }
+  return POLFED_OK;
+}
+
+// ------------------------------------------------------------ table kernels
+__global__ void k_tables_lo(const HamGeometry g, uint16_t* T_lo, uint16_t* U_lo, double* F_lo) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= (1 << g.b)) return;
+  uint32_t r = 0;
+  int k = 0;
+  for (int p = 0; p < g.b; p++)
+    if ((a >> p) & 1) r += c_binom[p][++k];
+  T_lo[a] = (uint16_t)r;
+  U_lo[g.cls_off[k] + r] = (uint16_t)a;
+  double d = 0.0;
+  const int nl = g.n_low1 + g.n_low2;
+  for (int q = 0; q < nl; q++) {
+    const double J = q < g.n_low1 ? g.J1 : g.J2;
+    d += J * g.Delta * (__popc(a & g.low_mask[q]) == 1 ? -0.25 : 0.25);
+  }
+  for (int i = 0; i < g.b; i++) d += g.h[i] * (((a >> i) & 1) ? 0.5 : -0.5);
+  F_lo[a] = d;
+}
+
+__global__ void k_tables_rec(const HamGeometry g, const uint16_t* T_lo, uint16_t* rec) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= (1 << g.b)) return;
+  const int RS = g.rec_stride;
+  uint16_t* r = rec + (size_t)(g.cls_off[__popc(a)] + T_lo[a]) * RS;
+  for (int e = 0; e < RS; e++) r[e] = 0xFFFF;
+  r[0] = (uint16_t)a;
+  const int nl = g.n_low1 + g.n_low2;
+  for (int k = 0; k < nl; k++) {
+    const uint32_t m = g.low_mask[k];
+    if (__popc((uint32_t)a & m) == 1) r[1 + k] = T_lo[a ^ m];
+  }
+  for (int k = 0; k < g.n_cross; k++) r[RS - 1 - k] = T_lo[a ^ (1 << g.cross_lo[k])];
+}
+
+__global__ void k_tables_hi(const HamGeometry g, int32_t* T_hi, double* F_hi) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= (1 << g.nh)) return;
+  const int n_lo = g.n_up - __popc(c);
+  if (n_lo < 0 || n_lo > g.b) {
+    T_hi[c] = -1;
+    F_hi[c] = 0.0;
+    return;
+  }
+  uint32_t r = 0;
+  int k = 0;
+  for (int q = 0; q < g.nh; q++)
+    if ((c >> q) & 1) r += c_binom[g.b + q][n_lo + (++k)];
+  T_hi[c] = (int32_t)r;
+  double d = 0.0;
+  const int nhb = g.n_high1 + g.n_high2;
+  for (int q = 0; q < nhb; q++) {
+    const double J = q < g.n_high1 ? g.J1 : g.J2;
+    d += J * g.Delta * (__popc(c & g.high_mask[q]) == 1 ? -0.25 : 0.25);
+  }
+  for (int i = 0; i < g.nh; i++) d += g.h[g.b + i] * (((c >> i) & 1) ? 0.5 : -0.5);
+  F_hi[c] = d;
+}
+
+__global__ void k_tables_cx(const HamGeometry g, double* C_x) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= (1 << g.n_cross)) return;
+  double d = 0.0;
+  for (int k = 0; k < g.n_cross; k++) {
+    const double J = g.cross_cls[k] == 1 ? g.J1 : g.J2;
+    d += J * g.Delta * (((p >> k) & 1) ? -0.25 : 0.25);
+  }
+  C_x[p] = d;
+}
+
+// --------------------------------------------------------- number policies
+struct KCf {
+  float cX, cH, cB, o1, o2;
+};
+struct KCd {
+  double cX, cH, cB, o1, o2;
+};
+struct KCdf {
+  float2 cX, cH, cB, o1, o2;
+};
+
+// Float-float arithmetic: a value is hi + lo with |lo| <= ulp(hi)/2.
+// two_sum: Knuth (TAOCP vol. 2, 4.2.2); fast_two_sum: Dekker (1971);
+// products use the FMA-based exact product error.
+__device__ __forceinline__ float2 fast_two_sum(float a, float b) {
+  float s = a + b;
+  float e = b - (s - a);
+  return make_float2(s, e);
+}
+__device__ __forceinline__ float2 two_sum(float a, float b) {
+  float s = a + b;
+  float bb = s - a;
+  float e = (a - (s - bb)) + (b - bb);
+  return make_float2(s, e);
+}
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+  float2 s = two_sum(a.x, b.x);
+  s.y += a.y + b.y;
+  return fast_two_sum(s.x, s.y);
+}
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
+  float p = a.x * b.x;
+  float e = fmaf(a.x, b.x, -p);
+  e = fmaf(a.x, b.y, e);
+  e = fmaf(a.y, b.x, e);
+  return fast_two_sum(p, e);
+}
+
+struct NF32 {
+  using S = float;
+  using C = float;
+  using A = float;
+  using KC = KCf;
+  static __device__ __forceinline__ A zero() { return 0.f; }
+  static __device__ __forceinline__ void acc(A& a, S v) { a += v; }
+  static __device__ __forceinline__ C add3(C a, C b, C c) { return a + b + c; }
+  static __device__ __forceinline__ S combine(S xv, S x1, S b2v, A a1, A a2, C ad, const KC& k, bool hx, bool hb,
+                                              bool j2) {
+    float y = ad * x1 + k.o1 * a1;
+    if (j2) y = fmaf(k.o2, a2, y);
+    float r = k.cH * y;
+    if (hx) r = fmaf(k.cX, xv, r);
+    if (hb) r = fmaf(k.cB, b2v, r);
+    return r;
+  }
+  static __device__ __forceinline__ float mag(S v) { return fabsf(v); }
+};
+
+struct NF64 {
+  using S = double;
+  using C = double;
+  using A = double;
+  using KC = KCd;
+  static __device__ __forceinline__ A zero() { return 0.0; }
+  static __device__ __forceinline__ void acc(A& a, S v) { a += v; }
+  static __device__ __forceinline__ C add3(C a, C b, C c) { return a + b + c; }
+  static __device__ __forceinline__ S combine(S xv, S x1, S b2v, A a1, A a2, C ad, const KC& k, bool hx, bool hb,
+                                              bool j2) {
+    double y = ad * x1 + k.o1 * a1;
+    if (j2) y = fma(k.o2, a2, y);
+    double r = k.cH * y;
+    if (hx) r = fma(k.cX, xv, r);
+    if (hb) r = fma(k.cB, b2v, r);
+    return r;
+  }
+  static __device__ __forceinline__ float mag(S v) { return (float)fabs(v); }
+};
+
+struct NDF {
+  using S = float2;  // (hi, lo)
+  using C = float2;
+  using A = float2;  // (running hi sum, accumulated low parts and rounding errors)
+  using KC = KCdf;
+  static __device__ __forceinline__ A zero() { return make_float2(0.f, 0.f); }
+  static __device__ __forceinline__ void acc(A& a, S v) {
+    float2 s = two_sum(a.x, v.x);
+    a.x = s.x;
+    a.y += s.y + v.y;
+  }
+  static __device__ __forceinline__ C add3(C a, C b, C c) { return df_add(df_add(a, b), c); }
+  static __device__ __forceinline__ S combine(S xv, S x1, S b2v, A a1, A a2, C ad, const KC& k, bool hx, bool hb,
+                                              bool j2) {
+    float2 y = df_add(df_mul(ad, x1), df_mul(k.o1, fast_two_sum(a1.x, a1.y)));
+    if (j2) y = df_add(y, df_mul(k.o2, fast_two_sum(a2.x, a2.y)));
+    float2 r = df_mul(k.cH, y);
+    if (hx) r = df_add(r, df_mul(k.cX, xv));
+    if (hb) r = df_add(r, df_mul(k.cB, b2v));
+    return r;
+  }
+  static __device__ __forceinline__ float mag(S v) { return fabsf(v.x); }
+};
+
+template <class S>
+union V16 {
+  int4 i;
+  S s[16 / sizeof(S)];
+};
+
+// ---------------------------------------------------------- the step kernel
+struct GroupInfo {
+  int r0, n_g, cls_base, n_hn1, n_hn;
+  int hn_base[kMaxBonds];
+  int cr_base[8], cr_need[8];
+};
+
+struct StepTables {
+  const uint16_t* rec;
+  const int32_t* T_hi;
+  const int32_t* order;
+  const void* F_lo;  // typed, alpha-scaled
+  const void* F_hi;  // typed, alpha-scaled, includes -alpha*beta
+  const void* C_x;   // typed, alpha-scaled
+};
+
+template <class NT, int LPR, bool J2>
+__global__ void __launch_bounds__(256) k_ham_step(const HamGeometry g, const StepTables t,
+                                                   const typename NT::S* __restrict__ b1,
+                                                   const typename NT::S* b2, const typename NT::S* __restrict__ x,
+                                                   typename NT::S* out, const typename NT::KC kc, int has_x,
+                                                   int has_b2) {
+  using S = typename NT::S;
+  using C = typename NT::C;
+  using A = typename NT::A;
+  constexpr int VEC = 16 / sizeof(S);
+  constexpr int W = VEC * LPR;
+  constexpr int MAXCR = J2 ? 6 : 2;  // cross bonds: (b-1,b), (L-1,0) and, with J2, four more
+  constexpr int HCH = 8;             // high-bond loads issued together per row
+  constexpr int RS = J2 ? 32 : 16;   // record entries
+  constexpr int LOWMAX = RS - 1 - MAXCR;
+  constexpr int LCH = 4;             // low-bond shared-memory gathers batched together
+
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int nlo_tab = 1 << g.b;
+  S* tile = reinterpret_cast<S*>(smem);
+  C* sFlo = reinterpret_cast<C*>(smem + (size_t)g.max_group * W * sizeof(S));
+  C* sCx = sFlo + nlo_tab;
+  __shared__ GroupInfo gi;
+  __shared__ C s_fhi;
+
+  const C* gFlo = reinterpret_cast<const C*>(t.F_lo);
+  const C* gFhi = reinterpret_cast<const C*>(t.F_hi);
+  const C* gCx = reinterpret_cast<const C*>(t.C_x);
+  for (int i = threadIdx.x; i < nlo_tab; i += blockDim.x) sFlo[i] = gFlo[i];
+  for (int i = threadIdx.x; i < (1 << g.n_cross); i += blockDim.x) sCx[i] = gCx[i];
+
+  const int warp = threadIdx.x >> 5, lane32 = threadIdx.x & 31;
+  const int unit = threadIdx.x / LPR, lane = threadIdx.x % LPR, units = blockDim.x / LPR;
+  const int n_cr = g.n_cross;
+  const int nlow = g.n_low1 + (J2 ? g.n_low2 : 0), nlow1 = g.n_low1;
+  int cr_lb[MAXCR], cr_c2[MAXCR];
+#pragma unroll
+  for (int k = 0; k < MAXCR; k++) {
+    cr_lb[k] = k < n_cr ? g.cross_lo[k] : 0;
+    cr_c2[k] = k < n_cr && g.cross_cls[k] == 2;
+  }
+
+  for (int gidx = blockIdx.x; gidx < g.n_groups; gidx += gridDim.x) {
+    const int grp = t.order[gidx];
+    __syncthreads();  // tables loaded / previous tile fully consumed
+    if (warp == 0) {
+      // high-bond neighbour groups (class-1 bonds listed first)
+      const int nhb = g.n_high1 + g.n_high2;
+      int cnt = 0, cnt1 = 0;
+      for (int k0 = 0; k0 < nhb; k0 += 32) {
+        const int k = k0 + lane32;
+        bool act = false;
+        int base = 0;
+        if (k < nhb) {
+          const uint32_t m = g.high_mask[k];
+          act = __popc((uint32_t)grp & m) == 1;
+          if (act) base = t.T_hi[grp ^ m];
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, act);
+        if (act) gi.hn_base[cnt + __popc(bal & ((1u << lane32) - 1u))] = base;
+        const unsigned m1 = (k0 + 32 <= g.n_high1) ? 0xffffffffu
+                            : (k0 >= g.n_high1)   ? 0u
+                                                  : ((1u << (g.n_high1 - k0)) - 1u);
+        cnt1 += __popc(bal & m1);
+        cnt += __popc(bal);
+      }
+      if (lane32 < n_cr) {
+        const int k = lane32;
+        gi.cr_need[k] = 1 - ((grp >> g.cross_hi[k]) & 1);  // the low bit must differ from the high bit
+        gi.cr_base[k] = t.T_hi[grp ^ (1 << g.cross_hi[k])];
+      }
+      if (lane32 == 0) {
+        const int n_lo = g.n_up - __popc(grp);
+        gi.r0 = t.T_hi[grp];
+        gi.n_g = (int)c_binom[g.b][n_lo];
+        gi.cls_base = g.cls_off[n_lo];
+        gi.n_hn1 = cnt1;
+        gi.n_hn = cnt;
+        s_fhi = gFhi[grp];
+      }
+    }
+    __syncthreads();
+    const int r0 = gi.r0, n_g = gi.n_g;
+    // stage the group's rows of b1 (contiguous: n_g * W elements)
+    {
+      const int4* src = reinterpret_cast<const int4*>(b1 + (size_t)r0 * W);
+      int4* dst = reinterpret_cast<int4*>(tile);
+      const int nchunk = n_g * LPR;
+      for (int c = threadIdx.x; c < nchunk; c += blockDim.x) dst[c] = __ldg(src + c);
+    }
+    // group constants in registers (read once, not per row)
+    const int n_hn = gi.n_hn, n_hn1 = gi.n_hn1, cls_base = gi.cls_base;
+    int hb[HCH];
+#pragma unroll
+    for (int k = 0; k < HCH; k++) hb[k] = gi.hn_base[k];
+    int cr_nd[MAXCR], cr_bs[MAXCR];
+#pragma unroll
+    for (int k = 0; k < MAXCR; k++) {
+      cr_nd[k] = k < n_cr ? gi.cr_need[k] : 2;  // 2 never matches a bit
+      cr_bs[k] = k < n_cr ? gi.cr_base[k] : 0;
+    }
+    const C fhi = s_fhi;
+    __syncthreads();
+    for (int loc = unit; loc < n_g; loc += units) {
+      // neighbour record of this row (shared by all groups of its class)
+      uint32_t rw[RS / 2];
+      {
+        const uint4* rp = reinterpret_cast<const uint4*>(t.rec + (size_t)(cls_base + loc) * RS);
+#pragma unroll
+        for (int q = 0; q < RS / 8; q++) {
+          const uint4 v = __ldg(rp + q);
+          rw[4 * q] = v.x;
+          rw[4 * q + 1] = v.y;
+          rw[4 * q + 2] = v.z;
+          rw[4 * q + 3] = v.w;
+        }
+      }
+#define PF_ENTRY(e) ((rw[(e) >> 1] >> (((e)&1) * 16)) & 0xFFFFu)
+      const uint32_t s_lo = PF_ENTRY(0);
+      const size_t off = (size_t)(r0 + loc) * W + lane * VEC;
+      // 1. issue every independent global load of this row first
+      V16<S> xv, bv;
+      if (has_x) xv.i = __ldcs(reinterpret_cast<const int4*>(x + off));
+      if (has_b2) bv.i = __ldcs(reinterpret_cast<const int4*>(b2 + off));
+      V16<S> hv[HCH];
+#pragma unroll
+      for (int k = 0; k < HCH; k++)
+        if (k < n_hn) hv[k].i = __ldg(reinterpret_cast<const int4*>(b1 + (size_t)(hb[k] + loc) * W + lane * VEC));
+      V16<S> cv[MAXCR];
+      uint32_t pattern = 0;
+#pragma unroll
+      for (int k = 0; k < MAXCR; k++) {
+        if ((int)((s_lo >> cr_lb[k]) & 1u) == cr_nd[k]) {
+          pattern |= 1u << k;
+          cv[k].i = __ldg(reinterpret_cast<const int4*>(b1 + (size_t)(cr_bs[k] + PF_ENTRY(RS - 1 - k)) * W + lane * VEC));
+        }
+      }
+      // 2. low bonds from shared memory while those loads are in flight
+      A a1[VEC], a2[VEC];
+#pragma unroll
+      for (int v = 0; v < VEC; v++) {
+        a1[v] = NT::zero();
+        a2[v] = NT::zero();
+      }
+#pragma unroll
+      for (int k0 = 0; k0 < LOWMAX; k0 += LCH) {
+        if (k0 < nlow) {
+          V16<S> u[LCH];
+          bool act[LCH];
+#pragma unroll
+          for (int i = 0; i < LCH; i++) {
+            const int k = k0 + i;
+            const uint32_t j = (k < LOWMAX) ? PF_ENTRY(1 + k) : 0xFFFFu;
+            act[i] = (k < nlow) && j != 0xFFFFu;
+            if (act[i]) u[i].i = *reinterpret_cast<const int4*>(tile + (size_t)j * W + lane * VEC);
+          }
+#pragma unroll
+          for (int i = 0; i < LCH; i++) {
+            if (act[i]) {
+              if (!J2 || k0 + i < nlow1) {
+#pragma unroll
+                for (int v = 0; v < VEC; v++) NT::acc(a1[v], u[i].s[v]);
+              } else {
+#pragma unroll
+                for (int v = 0; v < VEC; v++) NT::acc(a2[v], u[i].s[v]);
+              }
+            }
+          }
+        }
+      }
+#undef PF_ENTRY
+      // 3. consume the high-bond and cross-bond loads
+#pragma unroll
+      for (int k = 0; k < HCH; k++) {
+        if (k < n_hn) {
+          if (!J2 || k < n_hn1) {
+#pragma unroll
+            for (int v = 0; v < VEC; v++) NT::acc(a1[v], hv[k].s[v]);
+          } else {
+#pragma unroll
+            for (int v = 0; v < VEC; v++) NT::acc(a2[v], hv[k].s[v]);
+          }
+        }
+      }
+      for (int k = HCH; k < n_hn; k++) {  // rare: more than HCH active high bonds
+        V16<S> u;
+        u.i = __ldg(reinterpret_cast<const int4*>(b1 + (size_t)(gi.hn_base[k] + loc) * W + lane * VEC));
+        if (!J2 || k < n_hn1) {
+#pragma unroll
+          for (int v = 0; v < VEC; v++) NT::acc(a1[v], u.s[v]);
+        } else {
+#pragma unroll
+          for (int v = 0; v < VEC; v++) NT::acc(a2[v], u.s[v]);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < MAXCR; k++) {
+        if ((pattern >> k) & 1u) {
+          if (!J2 || !cr_c2[k]) {
+#pragma unroll
+            for (int v = 0; v < VEC; v++) NT::acc(a1[v], cv[k].s[v]);
+          } else {
+#pragma unroll
+            for (int v = 0; v < VEC; v++) NT::acc(a2[v], cv[k].s[v]);
+          }
+        }
+      }
+      const C ad = NT::add3(sFlo[s_lo], fhi, sCx[pattern]);
+      V16<S> xo, res;
+      xo.i = *reinterpret_cast<const int4*>(tile + (size_t)loc * W + lane * VEC);
+#pragma unroll
+      for (int v = 0; v < VEC; v++)
+        res.s[v] = NT::combine(has_x ? xv.s[v] : S(), xo.s[v], has_b2 ? bv.s[v] : S(), a1[v], a2[v], ad, kc,
+                               has_x, has_b2, J2);
+      __stcg(reinterpret_cast<int4*>(out + off), res.i);
+    }
+  }
+}
+
+// ------------------------------------------------------ slice conversions
+template <class NT>
+struct Conv;
+template <>
+struct Conv<NF32> {
+  static __device__ __forceinline__ float from_d(double v) { return (float)v; }
+  static __device__ __forceinline__ float from_f(float v) { return v; }
+  static __device__ __forceinline__ double to_d(float v) { return (double)v; }
+  static __device__ __forceinline__ float to_f(float v) { return v; }
+  static __device__ __forceinline__ float mul(float c, float v) { return c * v; }
+  static __device__ __forceinline__ float zero() { return 0.f; }
+};
+template <>
+struct Conv<NF64> {
+  static __device__ __forceinline__ double from_d(double v) { return v; }
+  static __device__ __forceinline__ double from_f(float v) { return (double)v; }
+  static __device__ __forceinline__ double to_d(double v) { return v; }
+  static __device__ __forceinline__ float to_f(double v) { return (float)v; }
+  static __device__ __forceinline__ double mul(double c, double v) { return c * v; }
+  static __device__ __forceinline__ double zero() { return 0.0; }
+};
+template <>
+struct Conv<NDF> {
+  static __device__ __forceinline__ float2 from_d(double v) {
+    const float hi = (float)v;
+    return make_float2(hi, (float)(v - (double)hi));
+  }
+  static __device__ __forceinline__ float2 from_f(float v) { return make_float2(v, 0.f); }
+  static __device__ __forceinline__ double to_d(float2 v) { return (double)v.x + (double)v.y; }
+  static __device__ __forceinline__ float to_f(float2 v) { return v.x + v.y; }
+  static __device__ __forceinline__ float2 mul(float2 c, float2 v) { return df_mul(c, v); }
+  static __device__ __forceinline__ float2 zero() { return make_float2(0.f, 0.f); }
+};
+
+// Load columns [col0, col0+ncols) of a row-major ABI block (ld elements per
+// row) into a slice buffer (zero padded to W columns), optionally also write a
+// scaled copy and a zero buffer; records max |x| in flag[0] (as float bits).
+template <class NT, class In>
+__global__ void k_slice_in(const In* __restrict__ in, int64_t dim, int ld, int col0, int ncols, int W,
+                           typename NT::S* xs, typename NT::S* a_scaled, typename NT::S* zero_buf,
+                           typename NT::C cscale, float* flag) {
+  using S = typename NT::S;
+  float mx = 0.f;
+  const int64_t n = dim * W;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / W;
+    const int c = (int)(e - r * W);
+    S v;
+    if (c < ncols) {
+      const In raw = in[r * ld + col0 + c];
+      if constexpr (sizeof(In) == 4) {
+        v = Conv<NT>::from_f(raw);
+        mx = fmaxf(mx, fabsf(raw));
+      } else {
+        v = Conv<NT>::from_d(raw);
+        mx = fmaxf(mx, (float)fabs(raw));
+      }
+    } else {
+      v = Conv<NT>::zero();
+    }
+    if (xs) xs[e] = v;
+    if (a_scaled) a_scaled[e] = Conv<NT>::mul(cscale, v);
+    if (zero_buf) zero_buf[e] = Conv<NT>::zero();
+  }
+  for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0 && flag) atomicMax(reinterpret_cast<int*>(flag), __float_as_int(mx));
+}
+
+// Slice buffer -> columns of a row-major ABI block; records max |y| in flag[1]
+// and sets flag[2] (int) to 1 on a non-finite value.
+template <class NT, class Out>
+__global__ void k_slice_out(const typename NT::S* __restrict__ ys, int64_t dim, int W, int ncols, Out* out, int ld,
+                            int col0, float* flag) {
+  float mx = 0.f;
+  int bad = 0;
+  const int64_t n = dim * ncols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / ncols;
+    const int c = (int)(e - r * ncols);
+    const typename NT::S v = ys[r * W + c];
+    if constexpr (sizeof(Out) == 4) {
+      const float f = Conv<NT>::to_f(v);
+      if (!isfinite(f)) bad = 1;
+      mx = fmaxf(mx, fabsf(f));
+      out[r * ld + col0 + c] = f;
+    } else {
+      const double d = Conv<NT>::to_d(v);
+      if (!isfinite(d)) bad = 1;
+      mx = fmaxf(mx, (float)fabs(d));
+      out[r * ld + col0 + c] = d;
+    }
+  }
+  for (int o = 16; o; o >>= 1) {
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+  }
+  if ((threadIdx.x & 31) == 0 && flag) {
+    atomicMax(reinterpret_cast<int*>(flag) + 1, __float_as_int(mx));
+    if (bad) atomicExch(reinterpret_cast<int*>(flag) + 2, 1);
+  }
+}
+
+// --------------------------------------------------------------- host side
+size_t elem_bytes(int kind) { return kind == POLFED_F32 ? 4 : 8; }
+int slice_width(int kind, int lpr) { return (int)(16 / elem_bytes(kind)) * lpr; }
+
+int choose_lpr(int kind, int n_b) {
+  const int vec = (int)(16 / elem_bytes(kind));
+  int lpr = 1;
+  while (lpr < 8 && vec * lpr < n_b) lpr *= 2;
+  return lpr;
+}
+
+static size_t typed_size(int kind) { return kind == POLFED_F64 ? 8 : (kind == POLFED_F32 ? 4 : 8); }
+
+int HamPlan::init(const polfed_model* m, cudaStream_t s, bool stream_ordered, int b_override) {
+  release();
+  upload_binomials();
+  PF_CHECK(build_geometry(m, b_override, &geo));
+  stream = s;
+  const size_t nlo = (size_t)1 << geo.b, nhi = (size_t)1 << geo.nh, ncx = (size_t)1 << geo.n_cross;
+  size_t bytes = 0;
+  auto carve = [&](size_t n) {
+    size_t o = bytes;
+    bytes += (n + 255) & ~(size_t)255;
+    return o;
+  };
+  const size_t oTlo = carve(nlo * 2), oUlo = carve(nlo * 2), oThi = carve(nhi * 4), oOrd = carve(nhi * 4),
+               oFlo = carve(nlo * 8), oFhi = carve(nhi * 8), oCx = carve(ncx * 8),
+               oRec = carve(nlo * (size_t)geo.rec_stride * 2);
+  stream_alloc = stream_ordered;
+  if (stream_ordered)
+    PF_CUDA(cudaMallocAsync(&dev, bytes, s));
+  else
+    PF_CUDA(cudaMalloc(&dev, bytes));
+  char* d = (char*)dev;
+  tab.T_lo = (uint16_t*)(d + oTlo);
+  tab.U_lo = (uint16_t*)(d + oUlo);
+  tab.T_hi = (int32_t*)(d + oThi);
+  tab.order = (int32_t*)(d + oOrd);
+  tab.F_lo = (double*)(d + oFlo);
+  tab.F_hi = (double*)(d + oFhi);
+  tab.C_x = (double*)(d + oCx);
+  tab.rec = (uint16_t*)(d + oRec);
+  k_tables_lo<<<(unsigned)((nlo + 255) / 256), 256, 0, s>>>(geo, tab.T_lo, tab.U_lo, tab.F_lo);
+  k_tables_rec<<<(unsigned)((nlo + 255) / 256), 256, 0, s>>>(geo, tab.T_lo, tab.rec);
+  k_tables_hi<<<(unsigned)((nhi + 255) / 256), 256, 0, s>>>(geo, tab.T_hi, tab.F_hi);
+  k_tables_cx<<<(unsigned)((ncx + 255) / 256), 256, 0, s>>>(geo, tab.C_x);
+  PF_CUDA(cudaGetLastError());
+  // group schedule: largest groups first (sizes depend only on popcount)
+  std::vector<int32_t> order;
+  order.reserve(geo.n_groups);
+  std::vector<std::pair<int, int>> cls;  // (size, popcount)
+  for (int pc = 0; pc <= geo.nh; pc++) {
+    int n_lo = geo.n_up - pc;
+    if (n_lo < 0 || n_lo > geo.b) continue;
+    cls.push_back({(int)binom_host(geo.b, n_lo), pc});
+  }
+  std::stable_sort(cls.begin(), cls.end(), [](auto& x, auto& y) { return x.first > y.first; });
+  for (auto& c : cls)
+    for (uint32_t grp = 0; grp < (uint32_t)nhi; grp++)
+      if (__builtin_popcount(grp) == c.second) order.push_back((int32_t)grp);
+  PF_CUDA(cudaMemcpyAsync(tab.order, order.data(), order.size() * 4, cudaMemcpyHostToDevice, s));
+  PF_CUDA(cudaStreamSynchronize(s));  // host vector goes out of scope
+  return POLFED_OK;
+}
+
+int HamPlan::prepare_typed(int kind, double e_lo, double e_hi) {
+  if (kind < 0 || kind > 2) return fail(POLFED_EINVAL, "bad dtype");
+  if (typed_ok[kind] && typed_lo[kind] == e_lo && typed_hi[kind] == e_hi) return POLFED_OK;
+  double alpha = 1.0, beta = 0.0;
+  if (!(e_lo == 0.0 && e_hi == 0.0)) {
+    if (!(e_hi > e_lo)) return fail(POLFED_EINVAL, "need e_lo < e_hi");
+    alpha = 2.0 / (e_hi - e_lo);
+    beta = 0.5 * (e_hi + e_lo);
+  }
+  const size_t nlo = (size_t)1 << geo.b, nhi = (size_t)1 << geo.nh, ncx = (size_t)1 << geo.n_cross;
+  const size_t es = typed_size(kind);
+  const size_t need = (nlo + nhi + ncx) * es + 512;
+  if (!typed[kind] || typed_bytes[kind] < need) {
+    if (typed[kind]) {
+      if (stream_alloc)
+        cudaFreeAsync(typed[kind], stream);
+      else
+        cudaFree(typed[kind]);
+      typed[kind] = nullptr;
+    }
+    if (stream_alloc)
+      PF_CUDA(cudaMallocAsync(&typed[kind], need, stream));
+    else
+      PF_CUDA(cudaMalloc(&typed[kind], need));
+    typed_bytes[kind] = need;
+  }
+  // scale on the host: copy the FP64 tables back (small), convert, upload
+  std::vector<double> flo(nlo), fhi(nhi), cx(ncx);
+  PF_CUDA(cudaMemcpyAsync(flo.data(), tab.F_lo, nlo * 8, cudaMemcpyDeviceToHost, stream));
+  PF_CUDA(cudaMemcpyAsync(fhi.data(), tab.F_hi, nhi * 8, cudaMemcpyDeviceToHost, stream));
+  PF_CUDA(cudaMemcpyAsync(cx.data(), tab.C_x, ncx * 8, cudaMemcpyDeviceToHost, stream));
+  PF_CUDA(cudaStreamSynchronize(stream));
+  std::vector<unsigned char> buf((nlo + nhi + ncx) * es);
+  size_t pos = 0;
+  auto put = [&](double v) {
+    if (kind == POLFED_F32) {
+      float f = (float)v;
+      memcpy(&buf[pos], &f, 4);
+    } else if (kind == POLFED_F64) {
+      memcpy(&buf[pos], &v, 8);
+    } else {
+      float hi = (float)v;
+      float lo = (float)(v - (double)hi);
+      memcpy(&buf[pos], &hi, 4);
+      memcpy(&buf[pos + 4], &lo, 4);
+    }
+    pos += es;
+  };
+  for (size_t i = 0; i < nlo; i++) put(alpha * flo[i]);
+  for (size_t i = 0; i < nhi; i++) put(alpha * (fhi[i] - beta));
+  for (size_t i = 0; i < ncx; i++) put(alpha * cx[i]);
+  PF_CUDA(cudaMemcpyAsync(typed[kind], buf.data(), buf.size(), cudaMemcpyHostToDevice, stream));
+  PF_CUDA(cudaStreamSynchronize(stream));
+  typed_ok[kind] = true;
+  typed_lo[kind] = e_lo;
+  typed_hi[kind] = e_hi;
+  return POLFED_OK;
+}
+
+void HamPlan::release() {
+  if (dev) {
+    if (stream_alloc)
+      cudaFreeAsync(dev, stream);
+    else
+      cudaFree(dev);
+  }
+  for (int k = 0; k < 3; k++) {
+    if (typed[k]) {
+      if (stream_alloc)
+        cudaFreeAsync(typed[k], stream);
+      else
+        cudaFree(typed[k]);
+    }
+    typed[k] = nullptr;
+    typed_bytes[k] = 0;
+    typed_ok[k] = false;
+  }
+  dev = nullptr;
+}
+
+static void split_df(double v, float2& o) {
+  o.x = (float)v;
+  o.y = (float)(v - (double)o.x);
+}
+
+template <class NT, int LPR, bool J2>
+static int launch_step_t(const HamPlan& p, const StepArgs& a, cudaStream_t s) {
+  if (p.geo.n_cross > (J2 ? 6 : 2)) return fail(POLFED_EINVAL, "more cross bonds than the kernel handles");
+  using S = typename NT::S;
+  using C = typename NT::C;
+  constexpr int W = (16 / sizeof(S)) * LPR;
+  const HamGeometry& g = p.geo;
+  const size_t smem = (size_t)g.max_group * W * sizeof(S) + (((size_t)1 << g.b) + ((size_t)1 << g.n_cross)) * sizeof(C);
+  auto kern = k_ham_step<NT, LPR, J2>;
+  static int configured_dev[64] = {0};
+  static size_t configured_smem[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 64 && !configured_dev[dev]) {
+    int optin = 0;
+    PF_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    cudaFuncAttributes fa;
+    PF_CUDA(cudaFuncGetAttributes(&fa, kern));
+    const int maxdyn = optin - (int)fa.sharedSizeBytes;
+    PF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, maxdyn));
+    configured_dev[dev] = 1;
+    configured_smem[dev] = (size_t)maxdyn;
+  }
+  if (dev < 64 && smem > configured_smem[dev]) return fail(POLFED_EINVAL, "slice tile does not fit in shared memory");
+  static int nsm_cache[64] = {0};
+  static size_t occ_smem[64] = {0};
+  static int occ_cache[64] = {0};
+  if (dev < 64 && !nsm_cache[dev]) cudaDeviceGetAttribute(&nsm_cache[dev], cudaDevAttrMultiProcessorCount, dev);
+  const int nsm = dev < 64 ? nsm_cache[dev] : 152;
+  const int threads = 256;
+  int occ = 1;
+  if (dev < 64 && occ_smem[dev] == smem && occ_cache[dev] > 0) {
+    occ = occ_cache[dev];
+  } else {
+    PF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem));
+    if (dev < 64) {
+      occ_smem[dev] = smem;
+      occ_cache[dev] = occ;
+    }
+  }
+  if (occ < 1) return fail(POLFED_EINVAL, "step kernel cannot be resident (shared memory)");
+  int grid = std::min(g.n_groups, nsm * occ);
+  StepTables t{p.tab.rec, p.tab.T_hi, p.tab.order, nullptr, nullptr, nullptr};
+  if (g.rec_stride != (J2 ? 32 : 16)) return fail(POLFED_EINVAL, "record layout does not match the kernel");
+  const size_t es = sizeof(C);
+  const char* base = (const char*)p.typed[std::is_same<NT, NF32>::value ? POLFED_F32 : (std::is_same<NT, NF64>::value ? POLFED_F64 : POLFED_DF64)];
+  t.F_lo = base;
+  t.F_hi = base + ((size_t)1 << g.b) * es;
+  t.C_x = base + (((size_t)1 << g.b) + ((size_t)1 << g.nh)) * es;
+  typename NT::KC kc;
+  const int kk = std::is_same<NT, NF32>::value ? POLFED_F32 : (std::is_same<NT, NF64>::value ? POLFED_F64 : POLFED_DF64);
+  const double alpha = (p.typed_lo[kk] == 0.0 && p.typed_hi[kk] == 0.0) ? 1.0 : 2.0 / (p.typed_hi[kk] - p.typed_lo[kk]);
+  const double o1 = alpha * 0.5 * g.J1, o2 = alpha * 0.5 * g.J2;
+  if constexpr (std::is_same<NT, NDF>::value) {
+    split_df(a.cX, kc.cX);
+    split_df(a.cH, kc.cH);
+    split_df(a.cB, kc.cB);
+    split_df(o1, kc.o1);
+    split_df(o2, kc.o2);
+  } else {
+    kc.cX = (C)a.cX;
+    kc.cH = (C)a.cH;
+    kc.cB = (C)a.cB;
+    kc.o1 = (C)o1;
+    kc.o2 = (C)o2;
+  }
+  kern<<<grid, threads, smem, s>>>(g, t, (const S*)a.b1, (const S*)a.b2, (const S*)a.x, (S*)a.out, kc,
+                                   a.cX != 0.0 && a.x != nullptr, a.cB != 0.0 && a.b2 != nullptr);
+  PF_CUDA(cudaGetLastError());
+  Counters& cn = counters();
+  cn.launches++;
+  cn.step_launches++;
+  cn.step_alg_bytes += (double)g.dim * W * sizeof(S) * (3.0 + (a.cX != 0.0 ? 1.0 : 0.0));
+  return POLFED_OK;
+}
+
+template <class NT>
+static int launch_step_n(const HamPlan& p, const StepArgs& a, cudaStream_t s) {
+  const bool j2 = p.geo.n_low2 + p.geo.n_high2 > 0 || p.geo.J2 != 0.0;
+  switch (a.lpr) {
+#define PF_CASE(L_)                                                               \
+  case L_:                                                                        \
+    return j2 ? launch_step_t<NT, L_, true>(p, a, s) : launch_step_t<NT, L_, false>(p, a, s);
+    PF_CASE(1)
+    PF_CASE(2)
+    PF_CASE(4)
+    PF_CASE(8)
+#undef PF_CASE
+    default:
+      return fail(POLFED_EINVAL, "unsupported lanes-per-row");
+  }
+}
+
+int launch_ham_step(const HamPlan& p, int kind, const StepArgs& a, cudaStream_t s) {
+  if (kind < 0 || kind > 2 || !p.typed_ok[kind]) return fail(POLFED_EINVAL, "operator tables not prepared for this precision");
+  switch (kind) {
+    case POLFED_F32:
+      return launch_step_n<NF32>(p, a, s);
+    case POLFED_F64:
+      return launch_step_n<NF64>(p, a, s);
+    case POLFED_DF64:
+      return launch_step_n<NDF>(p, a, s);
+  }
+  return fail(POLFED_EINVAL, "unknown dtype");
+}
+
+size_t filter_scratch_bytes(const HamPlan& plan, int kind, int lpr) {
+  const size_t slice = (size_t)plan.geo.dim * slice_width(kind, lpr) * elem_bytes(kind);
+  const size_t a = (slice + 255) & ~(size_t)255;
+  return 3 * a + 256;
+}
+
+static int ensure_scratch(FilterScratch& scr, size_t need, const HamPlan& plan, int kind, int lpr) {
+  if (scr.xs && scr.bytes >= need) return POLFED_OK;
+  return fail(POLFED_ENOMEM, "filter scratch too small");
+}
+
+static void carve_scratch(FilterScratch& scr, const HamPlan& plan, int kind, int lpr) {
+  const size_t slice = (size_t)plan.geo.dim * slice_width(kind, lpr) * elem_bytes(kind);
+  const size_t a = (slice + 255) & ~(size_t)255;
+  char* base = (char*)scr.xs;
+  scr.ba = base + a;
+  scr.bb = base + 2 * a;
+  scr.flag = (float*)(base + 3 * a);
+}
+
+template <class NT, class In>
+static int slice_in_t(const void* in, int64_t dim, int ld, int col0, int ncols, int W, void* xs, void* as,
+                      void* zb, double scale, float* flag, cudaStream_t s) {
+  typename NT::C cs;
+  if constexpr (std::is_same<NT, NDF>::value)
+    split_df(scale, cs);
+  else
+    cs = (typename NT::C)scale;
+  const int64_t n = dim * W;
+  int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16));
+  k_slice_in<NT, In><<<grid, 256, 0, s>>>((const In*)in, dim, ld, col0, ncols, W, (typename NT::S*)xs,
+                                           (typename NT::S*)as, (typename NT::S*)zb, cs, flag);
+  PF_CUDA(cudaGetLastError());
+  count_launch();
+  return POLFED_OK;
+}
+
+static int slice_in(int kind, int abi_kind, const void* in, int64_t dim, int ld, int col0, int ncols, int W,
+                    void* xs, void* as, void* zb, double scale, float* flag, cudaStream_t s) {
+  const bool f32in = abi_kind == POLFED_F32;
+  switch (kind) {
+    case POLFED_F32:
+      return f32in ? slice_in_t<NF32, float>(in, dim, ld, col0, ncols, W, xs, as, zb, scale, flag, s)
+                   : slice_in_t<NF32, double>(in, dim, ld, col0, ncols, W, xs, as, zb, scale, flag, s);
+    case POLFED_F64:
+      return f32in ? slice_in_t<NF64, float>(in, dim, ld, col0, ncols, W, xs, as, zb, scale, flag, s)
+                   : slice_in_t<NF64, double>(in, dim, ld, col0, ncols, W, xs, as, zb, scale, flag, s);
+    default:
+      return f32in ? slice_in_t<NDF, float>(in, dim, ld, col0, ncols, W, xs, as, zb, scale, flag, s)
+                   : slice_in_t<NDF, double>(in, dim, ld, col0, ncols, W, xs, as, zb, scale, flag, s);
+  }
+}
+
+template <class NT>
+static void slice_out_t(const void* ys, int64_t dim, int W, int ncols, void* out, bool f32out, int ld, int col0,
+                        float* flag, int grid, cudaStream_t s) {
+  if (f32out)
+    k_slice_out<NT, float><<<grid, 256, 0, s>>>((const typename NT::S*)ys, dim, W, ncols, (float*)out, ld, col0, flag);
+  else
+    k_slice_out<NT, double><<<grid, 256, 0, s>>>((const typename NT::S*)ys, dim, W, ncols, (double*)out, ld, col0,
+                                                  flag);
+}
+
+static int slice_out(int kind, int abi_kind, const void* ys, int64_t dim, int W, int ncols, void* out, int ld,
+                     int col0, float* flag, cudaStream_t s) {
+  const int64_t n = dim * ncols;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16));
+  const bool f32out = abi_kind == POLFED_F32;
+  if (kind == POLFED_F32)
+    slice_out_t<NF32>(ys, dim, W, ncols, out, f32out, ld, col0, flag, grid, s);
+  else if (kind == POLFED_F64)
+    slice_out_t<NF64>(ys, dim, W, ncols, out, f32out, ld, col0, flag, grid, s);
+  else
+    slice_out_t<NDF>(ys, dim, W, ncols, out, f32out, ld, col0, flag, grid, s);
+  PF_CUDA(cudaGetLastError());
+  count_launch();
+  return POLFED_OK;
+}
+
+// Device time of a run of step launches, by a pair of CUDA events on the launching stream.
+struct StepTimer {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaStream_t s;
+  explicit StepTimer(cudaStream_t st) : s(st) {
+    if (cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) cudaEventRecord(e0, s);
+  }
+  int stop() {
+    if (!e0 || !e1) return POLFED_OK;
+    PF_CUDA(cudaEventRecord(e1, s));
+    PF_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    PF_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    counters().step_gpu_s += 1e-3 * ms;
+    return POLFED_OK;
+  }
+  ~StepTimer() {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  }
+};
+
+int filter_block(HamPlan& plan, int kind, const double* c, int K, double invD, const void* in, void* out, int n_b,
+                 int abi_kind, FilterScratch& scr, cudaStream_t s, int lpr_hint) {
+  const int lpr = lpr_hint > 0 ? lpr_hint : choose_lpr(kind, n_b);
+  const int W = slice_width(kind, lpr);
+  PF_CHECK(ensure_scratch(scr, filter_scratch_bytes(plan, kind, lpr), plan, kind, lpr));
+  carve_scratch(scr, plan, kind, lpr);
+  const int64_t dim = plan.geo.dim;
+  PF_CUDA(cudaMemsetAsync(scr.flag, 0, 16, s));
+  for (int col0 = 0; col0 < n_b; col0 += W) {
+    const int ncols = std::min(W, n_b - col0);
+    if (K == 0) {
+      PF_CHECK(slice_in(kind, abi_kind, in, dim, n_b, col0, ncols, W, nullptr, scr.ba, nullptr, c[0] * invD,
+                        scr.flag, s));
+      PF_CHECK(slice_out(kind, abi_kind, scr.ba, dim, W, ncols, out, n_b, col0, scr.flag, s));
+      continue;
+    }
+    // b_K = c_K X (in ba), b_{K+1} = 0 (in bb)
+    PF_CHECK(slice_in(kind, abi_kind, in, dim, n_b, col0, ncols, W, scr.xs, scr.ba, scr.bb, c[K], scr.flag, s));
+    void* cur = scr.ba;  // b_{k+1}
+    void* oth = scr.bb;  // b_{k+2}, overwritten in place by b_k
+    StepTimer tm(s);
+    for (int k = K - 1; k >= 1; k--) {
+      StepArgs a{cur, oth, scr.xs, oth, c[k], 2.0, (k == K - 1) ? 0.0 : -1.0, lpr};
+      PF_CHECK(launch_ham_step(plan, kind, a, s));
+      std::swap(cur, oth);
+    }
+    // Y = (c_0 X + H~ b_1 - b_2) / D
+    StepArgs a{cur, oth, scr.xs, oth, c[0] * invD, invD, (K == 1) ? 0.0 : -invD, lpr};
+    PF_CHECK(launch_ham_step(plan, kind, a, s));
+    PF_CHECK(tm.stop());
+    PF_CHECK(slice_out(kind, abi_kind, oth, dim, W, ncols, out, n_b, col0, scr.flag, s));
+  }
+  return POLFED_OK;
+}
+
+int apply_block(HamPlan& plan, int kind, const void* in, void* out, int n_b, int abi_kind, FilterScratch& scr,
+                cudaStream_t s, int lpr_hint) {
+  const int lpr = lpr_hint > 0 ? lpr_hint : choose_lpr(kind, n_b);
+  const int W = slice_width(kind, lpr);
+  PF_CHECK(ensure_scratch(scr, filter_scratch_bytes(plan, kind, lpr), plan, kind, lpr));
+  carve_scratch(scr, plan, kind, lpr);
+  const int64_t dim = plan.geo.dim;
+  PF_CUDA(cudaMemsetAsync(scr.flag, 0, 16, s));
+  for (int col0 = 0; col0 < n_b; col0 += W) {
+    const int ncols = std::min(W, n_b - col0);
+    PF_CHECK(slice_in(kind, abi_kind, in, dim, n_b, col0, ncols, W, scr.xs, nullptr, nullptr, 0.0, scr.flag, s));
+    StepArgs a{scr.xs, nullptr, nullptr, scr.ba, 0.0, 1.0, 0.0, lpr};
+    PF_CHECK(launch_ham_step(plan, kind, a, s));
+    PF_CHECK(slice_out(kind, abi_kind, scr.ba, dim, W, ncols, out, n_b, col0, scr.flag, s));
+  }
+  return POLFED_OK;
+}
+
+void cheb_coeffs(double sigma, int K, std::vector<double>& c, double& D) {
+  // Eq. (2): c_n = sqrt(4 - 3 delta_{0n}) cos(n arccos sigma); D = sum_n c_n T_n(sigma)
+  // with T_n(sigma) = cos(n arccos sigma).  At sigma = 0, cos(n pi/2) is 0, +-1 exactly.
+  c.assign(K + 1, 0.0);
+  D = 0.0;
+  const double phi = std::acos(sigma);
+  for (int n = 0; n <= K; n++) {
+    double cn;
+    if (sigma == 0.0) {
+      cn = (n & 1) ? 0.0 : ((n / 2) & 1 ? -1.0 : 1.0);
+    } else {
+      cn = std::cos(n * phi);
+    }
+    c[n] = (n == 0 ? 1.0 : 2.0) * cn;
+    D += c[n] * cn;
+  }
+}
+
+// ------------------------------------------------------------- basis kernel
+// Unrank: the r-th L-bit string with n_up set bits in ascending order, by the
+// combinatorial number system (greedy from the top bit).
+__global__ void k_basis(int L, int n_up, uint32_t* states, int64_t dim) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < dim; r += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t rem = (uint32_t)r, s = 0;
+    int k = n_up;
+    for (int p = L - 1; p >= 0 && k > 0; p--) {
+      const uint32_t c = c_binom[p][k];  // states with the top set bit below p
+      if (rem >= c) {
+        s |= 1u << p;
+        rem -= c;
+        k--;
+      }
+    }
+    states[r] = s;
+  }
+}
+
+int launch_basis(int L, int n_up, uint32_t* d_states, int64_t dim, cudaStream_t s) {
+  upload_binomials();
+  if (dim == 0) return POLFED_OK;
+  int grid = (int)std::min<int64_t>((dim + 255) / 256, 152 * 32);
+  k_basis<<<grid, 256, 0, s>>>(L, n_up, d_states, dim);
+  PF_CUDA(cudaGetLastError());
+  return POLFED_OK;
+}
+
+}  // namespace polfed

@@ -1,0 +1,819 @@
+// Block Lanczos on P^K_sigma(H~) (Eqs. (3)-(4)) and the whole POLFED run.
+//
+//   U_j = P Q_j - Q_{j-1} B_j^T,  A_j = Q_j^T U_j,  R_{j+1} = U_j - Q_j A_j,  Q_{j+1} B_{j+1} = R_{j+1}
+//
+// with U_j re-orthogonalized against all of Q_1..Q_j "between (3) and (4)"
+// (block classical Gram-Schmidt, two passes; the first pass's Q_j block is
+// A_j and its Q_{j-1} block is B_j^T, since Q_j^T Q_{j-1} = 0), QR by
+// Cholesky QR applied twice, and the block tridiagonal
+// T_m = Q_m^T P Q_m (A_j on the diagonal, B_j below, B_j^T above).
+// Convergence: ||B_{j+1} t~_i|| for Ritz values theta_i >= p, t~_i the last
+// s components of the eigenvector t_i of T_m (text after Eq. (4)).
+// Ritz vectors u_i = Q_m t_i; eigenvalues u_i^T H~ u_i after a Rayleigh-Ritz
+// step with H~ on the span of the converged Ritz vectors; residuals
+// ||H~ u_i - eps_i u_i||.
+#include <cusolverDn.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "dense.h"
+#include "polfed_internal.h"
+
+using namespace polfed;
+
+namespace {
+
+bool debug_on() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = getenv("POLFED_DEBUG");
+    v = (e && e[0] == '1') ? 1 : 0;
+  }
+  return v == 1;
+}
+
+double now_s() {
+  using namespace std::chrono;
+  return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t n = 0;
+  int ensure(size_t need, size_t* total, size_t limit) {
+    if (p && n >= need) return POLFED_OK;
+    if (p) {
+      cudaFree(p);
+      if (total) *total -= n;
+    }
+    p = nullptr;
+    n = 0;
+    if (limit && total && *total + need > limit) return fail(POLFED_ENOMEM, "context workspace limit exceeded");
+    if (cudaMalloc(&p, need) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(POLFED_ENOMEM, "cudaMalloc of " + std::to_string(need) + " bytes failed");
+    }
+    n = need;
+    if (total) *total += need;
+    return POLFED_OK;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  template <class T>
+  T* as() const {
+    return (T*)p;
+  }
+};
+
+}  // namespace
+
+struct polfed_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  cusolverDnHandle_t solver = nullptr;
+  size_t ws_limit = 0, ws_total = 0;
+  polfed_opts opts;
+  bool have_opts = false;
+  DevBuf basis, U, R, fscr, ritz, small, evbuf, work, vecs;
+  Dense dense;
+  polfed_stats last;
+};
+
+namespace {
+
+struct ScopedDevice {
+  int prev = 0;
+  explicit ScopedDevice(int d) {
+    cudaGetDevice(&prev);
+    cudaSetDevice(d);
+  }
+  ~ScopedDevice() { cudaSetDevice(prev); }
+};
+
+// Symmetric eigen-solve of the n x n column-major matrix A (lda) on the
+// device with cuSOLVER (the projected problem); A is overwritten by the
+// eigenvectors, w receives the eigenvalues ascending.
+int syevd(polfed_ctx* c, double* A, int n, int lda, double* w) {
+  int lwork = 0;
+  if (cusolverDnDsyevd_bufferSize(c->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n, A, lda, w,
+                                  &lwork) != CUSOLVER_STATUS_SUCCESS)
+    return fail(POLFED_ECUDA, "cusolverDnDsyevd_bufferSize failed");
+  PF_CHECK(c->work.ensure((size_t)(lwork + 16) * sizeof(double), &c->ws_total, c->ws_limit));
+  int* info = (int*)(c->work.as<double>() + lwork);
+  if (cusolverDnDsyevd(c->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n, A, lda, w,
+                       c->work.as<double>(), lwork, info) != CUSOLVER_STATUS_SUCCESS)
+    return fail(POLFED_ECUDA, "cusolverDnDsyevd failed");
+  int hinfo = 0;
+  PF_CUDA(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  PF_CUDA(cudaStreamSynchronize(c->stream));
+  if (hinfo != 0) return fail(POLFED_ECUDA, "syevd info = " + std::to_string(hinfo));
+  return POLFED_OK;
+}
+
+int round_block(int n_b) {
+  if (n_b <= 16) return 16;
+  if (n_b <= 32) return 32;
+  if (n_b <= 64) return 64;
+  return 128;
+}
+
+// gather columns idx of a column-major matrix V (ld) into a column-major out (ld_out)
+__global__ void k_gather_cols(const double* V, int ld, const int* idx, int ncol, int nrow, double* out, int ld_out) {
+  const int64_t tot = (int64_t)ncol * nrow;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e / nrow), r = (int)(e % nrow);
+    out[(int64_t)c * ld_out + r] = V[(int64_t)idx[c] * ld + r];
+  }
+}
+
+// Exact mean and variance of the spectrum of the block: Tr H / N and
+// Tr H^2 / N - mean^2 = <d^2> + <sum of squared off-diagonals per row> - mean^2.
+__global__ void k_moments(const HamGeometry g, const uint16_t* U_lo, const int32_t* T_hi, const double* F_lo,
+                          const double* F_hi, const double* C_x, double* out) {
+  double s1 = 0.0, s2 = 0.0, so = 0.0;
+  const double w1 = 0.25 * g.J1 * g.J1, w2 = 0.25 * g.J2 * g.J2;
+  for (int grp = blockIdx.x; grp < (1 << g.nh); grp += gridDim.x) {
+    if (T_hi[grp] < 0) continue;
+    const int n_lo = g.n_up - __popc(grp);
+    const int n_g = g.cls_off[n_lo + 1] - g.cls_off[n_lo];
+    for (int loc = threadIdx.x; loc < n_g; loc += blockDim.x) {
+      const uint32_t s_lo = U_lo[g.cls_off[n_lo] + loc];
+      uint32_t pattern = 0;
+      double off = 0.0;
+      for (int k = 0; k < g.n_cross; k++) {
+        const int hb = (grp >> g.cross_hi[k]) & 1;
+        if ((int)((s_lo >> g.cross_lo[k]) & 1) != hb) {
+          pattern |= 1u << k;
+          off += g.cross_cls[k] == 1 ? w1 : w2;
+        }
+      }
+      for (int k = 0; k < g.n_low1 + g.n_low2; k++)
+        if (__popc(s_lo & g.low_mask[k]) == 1) off += k < g.n_low1 ? w1 : w2;
+      for (int k = 0; k < g.n_high1 + g.n_high2; k++)
+        if (__popc((uint32_t)grp & g.high_mask[k]) == 1) off += k < g.n_high1 ? w1 : w2;
+      const double d = F_lo[s_lo] + F_hi[grp] + C_x[pattern];
+      s1 += d;
+      s2 += d * d;
+      so += off;
+    }
+  }
+  atomicAdd(out + 0, s1);
+  atomicAdd(out + 1, s2);
+  atomicAdd(out + 2, so);
+}
+
+double lobe_root(double p) {
+  // first positive root of sin(y)/y = p (main lobe of the Dirichlet kernel)
+  double a = 1e-6, b = M_PI;
+  for (int i = 0; i < 200; i++) {
+    double m = 0.5 * (a + b);
+    if (std::sin(m) / m > p)
+      a = m;
+    else
+      b = m;
+  }
+  return 0.5 * (a + b);
+}
+
+struct LanczosParams {
+  double e_lo, e_hi, sigma;
+  int K, S, N_ev;
+  polfed_opts o;
+  double tol_resid_t;  // acceptance threshold on ||H~ u - eps u||
+  bool accept_any;     // accept the first verified set (FP32 stage before refinement)
+};
+
+struct LanczosOut {
+  std::vector<double> evals_t;  // H~ units, ascending
+  std::vector<double> resid_t;  // H~ units
+  int n_out = 0, m = 0, n_conv = 0, checks = 0;
+  int64_t matvec_cols = 0;
+  double t_filter = 0, t_reorth = 0, t_qr = 0, t_teig = 0, t_ritz = 0;
+};
+
+int extract(polfed_ctx* c, HamPlan& plan, const LanczosParams& P, const double* Qb, int m_done,
+            const std::vector<double>& theta, const std::vector<double>& tres, double tol_sel, double* d_evecs,
+            LanczosOut& out);
+
+int run_lanczos(polfed_ctx* c, HamPlan& plan, const LanczosParams& P, double* d_evecs, LanczosOut& out) {
+  cudaStream_t s = c->stream;
+  const int64_t dim = plan.geo.dim;
+  const int S = P.S;
+  const int kind = P.o.precision == POLFED_F32 ? POLFED_F32 : (P.o.precision == POLFED_F64 ? POLFED_F64 : POLFED_DF64);
+  if (P.N_ev < 1 || P.N_ev > dim) return fail(POLFED_EINVAL, "N_ev must be in 1..dim");
+  int m_max = (int)std::ceil(P.o.cols_factor * (1.0 + P.o.k_margin) * P.N_ev / S) + 1;
+  // block Lanczos needs polynomial degree (steps) as well as columns: with few
+  // wanted pairs per block column the degree, not ms ~ 2 N_ev, limits convergence
+  m_max = std::max(m_max, 24);
+  m_max = (int)std::min<int64_t>(m_max, dim / S);
+  if (m_max < 1) return fail(POLFED_EINVAL, "dimension too small for this block size");
+  Dense& D = c->dense;
+  D.dim = dim;
+  D.S = S;
+  PF_CHECK(D.configure());
+  const int64_t pstride = dim * S;
+  PF_CHECK(c->basis.ensure((size_t)(m_max + 1) * pstride * sizeof(double), &c->ws_total, c->ws_limit));
+  PF_CHECK(c->U.ensure((size_t)pstride * sizeof(double), &c->ws_total, c->ws_limit));
+  const int lpr = choose_lpr(kind, S);
+  PF_CHECK(c->fscr.ensure(filter_scratch_bytes(plan, kind, lpr), &c->ws_total, c->ws_limit));
+  PF_CHECK(plan.prepare_typed(kind, P.e_lo, P.e_hi));
+  FilterScratch scr;
+  scr.xs = c->fscr.p;
+  scr.bytes = c->fscr.n;
+  std::vector<double> coef;
+  double Dn = 1.0;
+  cheb_coeffs(P.sigma, P.K, coef, Dn);
+  const double invD = 1.0 / Dn;
+  double* Qb = c->basis.as<double>();
+  double* Ub = c->U.as<double>();
+  // Q_1: random orthonormal N x s
+  PF_CHECK(D.random_fill(Qb, pstride, P.o.seed, s));
+  bool brk = false;
+  PF_CHECK(D.cholqr(Qb, Qb, nullptr, 2, s, &brk));
+  if (brk) return fail(POLFED_ECUDA, "random start block is rank deficient");
+  std::vector<std::vector<double>> A, B;  // A_j, B_{j+1} (row-major S x S)
+  // device buffers for projections (max (m_max+1) S x S) and T
+  const size_t cmax = (size_t)(m_max + 1) * S * S;
+  PF_CHECK(c->small.ensure((cmax + 16) * sizeof(double), &c->ws_total, c->ws_limit));
+  double* Cdev = c->small.as<double>();
+  std::vector<double> Chost((size_t)S * S);
+  std::vector<double> theta, tres;
+  std::vector<int> conv_idx;
+  int status = POLFED_OK;
+  int m_done = 0;
+  bool stopped = false;
+  const double p = P.o.p;
+  double tol_cur = P.o.tol_conv;
+  std::vector<double> colnrm(S);
+  for (int j = 0; j < m_max; j++) {
+    double* Qj = Qb + (int64_t)j * pstride;
+    double t0 = now_s();
+    PF_CHECK(filter_block(plan, kind, coef.data(), P.K, invD, Qj, Ub, S, POLFED_F64, scr, s, lpr));
+    PF_CHECK(D.coldot(Ub, Ub, S, colnrm.data(), s));  // synchronizes
+    out.matvec_cols += (int64_t)P.K * S;
+    double t1 = now_s();
+    out.t_filter += t1 - t0;
+    for (int q = 0; q < S; q++)
+      if (!std::isfinite(colnrm[q]) || colnrm[q] > 1.0 + 1e-6)
+        return fail(POLFED_EBOUNDS, "filtered block norm exceeds 1: spectrum outside [e_lo, e_hi]");
+    // pass 1: C = Q_{0..j}^T U; A_j = sym(C_j); U -= Q C
+    PF_CHECK(D.gram(Qb, pstride, j + 1, Ub, Cdev, S, 0, s));
+    PF_CUDA(cudaMemcpyAsync(Chost.data(), Cdev + (size_t)j * S * S, (size_t)S * S * sizeof(double),
+                            cudaMemcpyDeviceToHost, s));
+    PF_CHECK(D.update(Qb, pstride, j + 1, Cdev, S, 1, S, Ub, 0, -1.0, 1.0, s));
+    // pass 2
+    PF_CHECK(D.gram(Qb, pstride, j + 1, Ub, Cdev, S, 0, s));
+    PF_CHECK(D.update(Qb, pstride, j + 1, Cdev, S, 1, S, Ub, 0, -1.0, 1.0, s));
+    PF_CUDA(cudaStreamSynchronize(s));
+    std::vector<double> Aj((size_t)S * S);
+    for (int a = 0; a < S; a++)
+      for (int b = 0; b < S; b++) Aj[(size_t)a * S + b] = 0.5 * (Chost[(size_t)a * S + b] + Chost[(size_t)b * S + a]);
+    A.push_back(Aj);
+    double t2 = now_s();
+    out.t_reorth += t2 - t1;
+    // QR: Q_{j+1} B_{j+1} = R
+    std::vector<double> Bn((size_t)S * S);
+    double* Qn = Qb + (int64_t)(j + 1) * pstride;
+    PF_CHECK(D.cholqr(Ub, Qn, Bn.data(), 2, s, &brk));
+    B.push_back(Bn);
+    if (debug_on()) {
+      // orthogonality of the new panel against Q_0 and itself
+      double* Ct = Cdev;
+      std::vector<double> h((size_t)S * S), h0((size_t)S * S);
+      PF_CHECK(D.gram(Qn, 0, 1, Qn, Ct, S, 0, s));
+      PF_CUDA(cudaMemcpyAsync(h.data(), Ct, (size_t)S * S * 8, cudaMemcpyDeviceToHost, s));
+      PF_CUDA(cudaStreamSynchronize(s));
+      PF_CHECK(D.gram(Qb, 0, 1, Qn, Ct, S, 0, s));
+      PF_CUDA(cudaMemcpyAsync(h0.data(), Ct, (size_t)S * S * 8, cudaMemcpyDeviceToHost, s));
+      PF_CUDA(cudaStreamSynchronize(s));
+      double e1 = 0, e0 = 0, bn = 0, tr = 0, cm = 0;
+      for (int a = 0; a < S; a++)
+        for (int b = 0; b < S; b++) {
+          e1 = std::max(e1, std::fabs(h[(size_t)a * S + b] - (a == b)));
+          e0 = std::max(e0, std::fabs(h0[(size_t)a * S + b]));
+          bn += Bn[(size_t)a * S + b] * Bn[(size_t)a * S + b];
+        }
+      for (int a = 0; a < S; a++) tr += Aj[(size_t)a * S + a], cm = std::max(cm, colnrm[a]);
+      fprintf(stderr, "[polfed dbg] j=%d  max|U col|^2=%.3e  trA=%.4e  |B|_F=%.3e  |QnQn-I|=%.2e  |Q0Qn|=%.2e\n", j, cm,
+              tr, std::sqrt(bn), e1, e0);
+    }
+    double t3 = now_s();
+    out.t_qr += t3 - t2;
+    m_done = j + 1;
+    if (brk) {
+      status = fail(POLFED_ENOCONV, "Lanczos breakdown (rank-deficient residual block)");
+      break;
+    }
+    // convergence check
+    const int n = m_done * S;
+    const bool last = (j == m_max - 1);
+    if (n < (int)((1.0 + P.o.k_margin) * P.N_ev) && !last) continue;
+    std::vector<double> T((size_t)n * n, 0.0);  // column-major, symmetric
+    for (int i = 0; i < m_done; i++) {
+      for (int a = 0; a < S; a++)
+        for (int b = 0; b < S; b++) T[(size_t)(i * S + b) * n + i * S + a] = A[i][(size_t)a * S + b];
+      if (i + 1 < m_done)
+        for (int a = 0; a < S; a++)
+          for (int b = 0; b < S; b++) {
+            const double v = B[i][(size_t)a * S + b];  // B_{i+1}: block (i+1, i)
+            T[(size_t)(i * S + b) * n + (i + 1) * S + a] = v;
+            T[(size_t)((i + 1) * S + a) * n + i * S + b] = v;
+          }
+    }
+    PF_CHECK(c->evbuf.ensure(((size_t)n * n + n) * sizeof(double), &c->ws_total, c->ws_limit));
+    double* Td = c->evbuf.as<double>();
+    double* wd = Td + (size_t)n * n;
+    PF_CUDA(cudaMemcpyAsync(Td, T.data(), (size_t)n * n * sizeof(double), cudaMemcpyHostToDevice, s));
+    PF_CHECK(syevd(c, Td, n, n, wd));
+    out.checks++;
+    theta.assign(n, 0.0);
+    PF_CUDA(cudaMemcpyAsync(theta.data(), wd, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    // last S rows of every eigenvector
+    std::vector<double> tail((size_t)S * n);
+    PF_CUDA(cudaMemcpy2DAsync(tail.data(), S * sizeof(double), Td + (size_t)(m_done - 1) * S, (size_t)n * sizeof(double),
+                              S * sizeof(double), n, cudaMemcpyDeviceToHost, s));
+    PF_CUDA(cudaStreamSynchronize(s));
+    tres.assign(n, 0.0);
+    const std::vector<double>& Bl = B.back();
+    for (int i = 0; i < n; i++) {
+      double ss = 0.0;
+      for (int a = 0; a < S; a++) {
+        double v = 0.0;
+        for (int b = 0; b < S; b++) v += Bl[(size_t)a * S + b] * tail[(size_t)i * S + b];
+        ss += v * v;
+      }
+      tres[i] = std::sqrt(ss);
+    }
+    out.t_teig += now_s() - t3;
+    // stopping rule: the N_ev largest Ritz values are >= p and all converged
+    std::vector<int> ord(n);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::sort(ord.begin(), ord.end(), [&](int x, int y) { return theta[x] > theta[y]; });
+    int nconv_p = 0;
+    for (int i = 0; i < n; i++)
+      if (theta[i] >= p && tres[i] <= tol_cur) nconv_p++;
+    const bool ok_theta = n >= P.N_ev && theta[ord[P.N_ev - 1]] >= p;  // N_ev accessible values found
+    double maxres_top = 0.0;
+    for (int k = 0; k < std::min(n, P.N_ev); k++) maxres_top = std::max(maxres_top, tres[ord[k]]);
+    const bool ok = ok_theta && maxres_top <= tol_cur;
+    out.n_conv = nconv_p;
+    if (debug_on()) {
+      fprintf(stderr, "[polfed dbg] check n=%d: top theta/res:", n);
+      for (int k = 0; k < std::min(n, 12); k++) fprintf(stderr, " %.4f/%.1e", theta[ord[k]], tres[ord[k]]);
+      fprintf(stderr, "\n   around N_ev:");
+      for (int k = std::max(0, P.N_ev - 4); k < std::min(n, P.N_ev + 4); k++)
+        fprintf(stderr, " %.4f/%.1e", theta[ord[k]], tres[ord[k]]);
+      fprintf(stderr, "\n");
+    }
+    if (P.o.verbose)
+      fprintf(stderr, "[polfed] step %d  cols %d  n_conv(theta>=p) %d  theta_Nev %.4f  max_res_top %.2e\n", j + 1, n,
+              nconv_p, n >= P.N_ev ? theta[ord[P.N_ev - 1]] : -1.0,
+              [&] {
+                double mr = 0;
+                for (int k = 0; k < std::min(n, P.N_ev); k++) mr = std::max(mr, tres[ord[k]]);
+                return mr;
+              }());
+    if (ok || (last && ok_theta)) {
+      // verify by the residuals of the Rayleigh-Ritz pairs (text after Eq. (4))
+      const double t5 = now_s();
+      const double tol_sel = std::max(tol_cur, maxres_top);  // all N_ev top pairs, plus converged guards
+      const int erc = extract(c, plan, P, Qb, m_done, theta, tres, tol_sel, d_evecs, out);
+      out.t_ritz += now_s() - t5;
+      if (erc != POLFED_OK) return erc;
+      double mr = 0.0;
+      for (double r : out.resid_t) mr = std::max(mr, r);
+      if (P.o.verbose || debug_on())
+        fprintf(stderr, "[polfed] verify at step %d: %d pairs, max resid (H~) %.3e, target %.3e\n", j + 1, out.n_out, mr,
+                P.tol_resid_t);
+      if (out.n_out >= P.N_ev && (mr <= P.tol_resid_t || P.accept_any)) {
+        stopped = true;
+        break;
+      }
+      tol_cur = 0.1 * std::min(tol_cur, maxres_top);  // not accurate enough yet: demand smaller Ritz residuals
+    }
+  }
+  out.m = m_done;
+  if (!stopped && status == POLFED_OK) status = fail(POLFED_ENOCONV, "column budget exhausted before convergence");
+  if (status == POLFED_OK && out.n_out < P.N_ev) status = fail(POLFED_ENOCONV, "fewer converged pairs than requested");
+  return status;
+}
+
+// Ritz vectors of the converged pairs (theta >= p - 0.02, ||B t~|| <= tol_sel),
+// Rayleigh-Ritz with H~ on their span, the N_ev pairs nearest sigma, residuals.
+// The Lanczos basis is left intact (outputs live in the ritz buffer).
+int extract(polfed_ctx* c, HamPlan& plan, const LanczosParams& P, const double* Qb, int m_done,
+            const std::vector<double>& theta, const std::vector<double>& tres, double tol_sel, double* d_evecs,
+            LanczosOut& out) {
+  cudaStream_t s = c->stream;
+  Dense& D = c->dense;
+  const int64_t dim = plan.geo.dim;
+  const int S = P.S;
+  const int64_t pstride = dim * S;
+  const int n = m_done * S;
+  const double p_rr = P.o.p - 0.02;
+  std::vector<int> conv_idx;
+  for (int i = 0; i < n; i++)
+    if (theta[i] >= p_rr && tres[i] <= tol_sel) conv_idx.push_back(i);
+  if (conv_idx.empty()) {
+    out.n_out = 0;
+    out.evals_t.clear();
+    out.resid_t.clear();
+    return POLFED_OK;
+  }
+  const int nr = (int)conv_idx.size();
+  const int npan = (nr + S - 1) / S;
+  const int nr_pad = npan * S;
+  const int nout = std::min(nr, P.N_ev);
+  const int opan = (nout + S - 1) / S;
+  // T eigenvectors are in c->evbuf (column-major n x n)
+  double* Td = c->evbuf.as<double>();
+  PF_CHECK(c->vecs.ensure(((size_t)n * nr_pad + 64) * sizeof(double) + (size_t)nr_pad * sizeof(int), &c->ws_total,
+                          c->ws_limit));
+  double* Vsel = c->vecs.as<double>();
+  int* idx_d = (int*)(Vsel + (size_t)n * nr_pad + 64);
+  PF_CUDA(cudaMemcpyAsync(idx_d, conv_idx.data(), nr * sizeof(int), cudaMemcpyHostToDevice, s));
+  k_gather_cols<<<1024, 256, 0, s>>>(Td, n, idx_d, nr, n, Vsel, n);
+  PF_CUDA(cudaGetLastError());
+  count_launch();
+  PF_CHECK(c->ritz.ensure((size_t)(2 * nr_pad + 2 * opan * S) * dim * sizeof(double), &c->ws_total, c->ws_limit));
+  double* Ur = c->ritz.as<double>();          // nr_pad columns, panel-major
+  double* Wr = Ur + (size_t)nr_pad * dim;      // H~ Ur
+  double* Uo = Wr + (size_t)nr_pad * dim;      // selected eigenvectors
+  double* Wo = Uo + (size_t)opan * pstride;    // their images
+  PF_CHECK(D.update(Qb, pstride, m_done, Vsel, 1, n, nr, Ur, pstride, 1.0, 0.0, s));
+  // W = H~ U in FP64, panel by panel
+  PF_CHECK(plan.prepare_typed(POLFED_F64, P.e_lo, P.e_hi));
+  const int lpr64 = choose_lpr(POLFED_F64, S);
+  PF_CHECK(c->fscr.ensure(std::max(c->fscr.n, filter_scratch_bytes(plan, POLFED_F64, lpr64)), &c->ws_total,
+                          c->ws_limit));
+  FilterScratch scr64;
+  scr64.xs = c->fscr.p;
+  scr64.bytes = c->fscr.n;
+  for (int q = 0; q < npan; q++)
+    PF_CHECK(apply_block(plan, POLFED_F64, Ur + (size_t)q * pstride, Wr + (size_t)q * pstride, S, POLFED_F64, scr64, s,
+                         lpr64));
+  out.matvec_cols += nr_pad;
+  // G = U^T W (nr_pad x nr_pad); the eigen-solve of its leading nr x nr block
+  PF_CHECK(c->evbuf.ensure(((size_t)nr_pad * nr_pad + nr_pad) * sizeof(double), &c->ws_total, c->ws_limit));
+  double* G = c->evbuf.as<double>();
+  double* lam = G + (size_t)nr_pad * nr_pad;
+  for (int q = 0; q < npan; q++) PF_CHECK(D.gram(Ur, pstride, npan, Wr + (size_t)q * pstride, G, nr_pad, q * S, s));
+  PF_CHECK(syevd(c, G, nr, nr_pad, lam));
+  std::vector<double> lamh(nr);
+  PF_CUDA(cudaMemcpyAsync(lamh.data(), lam, nr * sizeof(double), cudaMemcpyDeviceToHost, s));
+  PF_CUDA(cudaStreamSynchronize(s));
+  // the N_ev nearest sigma, ascending
+  std::vector<int> sel(nr);
+  std::iota(sel.begin(), sel.end(), 0);
+  std::stable_sort(sel.begin(), sel.end(),
+                   [&](int x, int y) { return std::fabs(lamh[x] - P.sigma) < std::fabs(lamh[y] - P.sigma); });
+  sel.resize(nout);
+  std::sort(sel.begin(), sel.end());
+  PF_CUDA(cudaMemcpyAsync(idx_d, sel.data(), nout * sizeof(int), cudaMemcpyHostToDevice, s));
+  // rows nr..nr_pad-1 multiply the zero padding columns of Ur/Wr: make them 0, not stale memory
+  PF_CUDA(cudaMemsetAsync(Vsel, 0, (size_t)nr_pad * nout * sizeof(double), s));
+  k_gather_cols<<<1024, 256, 0, s>>>(G, nr_pad, idx_d, nout, nr, Vsel, nr_pad);
+  PF_CUDA(cudaGetLastError());
+  count_launch();
+  PF_CHECK(D.update(Ur, pstride, npan, Vsel, 1, nr_pad, nout, Uo, pstride, 1.0, 0.0, s));
+  PF_CHECK(D.update(Wr, pstride, npan, Vsel, 1, nr_pad, nout, Wo, pstride, 1.0, 0.0, s));
+  std::vector<double> lsel(opan * S, 0.0);
+  for (int i = 0; i < nout; i++) lsel[i] = lamh[sel[i]];
+  double* lsel_d = lam;  // reuse
+  PF_CUDA(cudaMemcpyAsync(lsel_d, lsel.data(), lsel.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+  out.evals_t.assign(nout, 0.0);
+  out.resid_t.assign(nout, 0.0);
+  std::vector<double> rn(S);
+  for (int q = 0; q < opan; q++) {
+    PF_CHECK(D.resid(Uo + (size_t)q * pstride, Wo + (size_t)q * pstride, lsel_d + q * S, s));
+    PF_CHECK(D.coldot(Wo + (size_t)q * pstride, Wo + (size_t)q * pstride, S, rn.data(), s));
+    for (int k = 0; k < S && q * S + k < nout; k++) out.resid_t[q * S + k] = std::sqrt(std::max(0.0, rn[k]));
+  }
+  for (int i = 0; i < nout; i++) out.evals_t[i] = lsel[i];
+  if (d_evecs) PF_CHECK(D.panels_to_colmajor(Uo, nout, d_evecs, s));
+  PF_CUDA(cudaStreamSynchronize(s));
+  out.n_out = nout;
+  return POLFED_OK;
+}
+
+// Single-vector Lanczos on H for E_min and E_max (text before Eq. (3)).
+int spectral_bounds(polfed_ctx* c, HamPlan& plan, const polfed_opts& o, double* emin, double* emax, double* err,
+                    int64_t* matvecs) {
+  cudaStream_t s = c->stream;
+  const int64_t dim = plan.geo.dim;
+  PF_CHECK(plan.prepare_typed(POLFED_F64, 0.0, 0.0));
+  const int lpr = choose_lpr(POLFED_F64, 1);
+  PF_CHECK(c->fscr.ensure(std::max(c->fscr.n, filter_scratch_bytes(plan, POLFED_F64, lpr)), &c->ws_total, c->ws_limit));
+  FilterScratch scr;
+  scr.xs = c->fscr.p;
+  scr.bytes = c->fscr.n;
+  PF_CHECK(c->R.ensure((size_t)3 * dim * sizeof(double), &c->ws_total, c->ws_limit));
+  double* v0 = c->R.as<double>();
+  double* v1 = v0 + dim;
+  double* w = v1 + dim;
+  Dense& D = c->dense;
+  D.dim = dim;
+  PF_CHECK(D.random_fill(v1, dim, o.seed ^ 0x5bd1e995ull, s));
+  double nrm = 0.0;
+  PF_CHECK(D.coldot(v1, v1, 1, &nrm, s));
+  PF_CHECK(D.axpbypcz(dim, 0.0, v1, 1.0 / std::sqrt(nrm), v1, 0.0, nullptr, s));
+  PF_CUDA(cudaMemsetAsync(v0, 0, dim * sizeof(double), s));
+  std::vector<double> al, be;  // be[k] couples k and k+1
+  double beta = 0.0;
+  const int kmax = (int)std::min<int64_t>(o.bounds_steps, dim);
+  double lo = 0, hi = 0, e_lo = 1e300, e_hi = 1e300;
+  for (int k = 0; k < kmax; k++) {
+    PF_CHECK(apply_block(plan, POLFED_F64, v1, w, 1, POLFED_F64, scr, s, lpr));
+    (*matvecs)++;
+    double a = 0.0;
+    PF_CHECK(D.coldot(v1, w, 1, &a, s));
+    al.push_back(a);
+    PF_CHECK(D.axpbypcz(dim, -a, v1, 1.0, w, -beta, v0, s));
+    double bb = 0.0;
+    PF_CHECK(D.coldot(w, w, 1, &bb, s));
+    beta = std::sqrt(std::max(bb, 0.0));
+    be.push_back(beta);
+    const int m = k + 1;
+    const bool check = (m >= 20 && m % 20 == 0) || m == kmax || beta < 1e-300;
+    if (check) {
+      // eigen-solve of the m x m tridiagonal
+      std::vector<double> T((size_t)m * m, 0.0);
+      for (int i = 0; i < m; i++) {
+        T[(size_t)i * m + i] = al[i];
+        if (i + 1 < m) T[(size_t)i * m + i + 1] = T[(size_t)(i + 1) * m + i] = be[i];
+      }
+      PF_CHECK(c->evbuf.ensure(((size_t)m * m + m) * sizeof(double), &c->ws_total, c->ws_limit));
+      double* Td = c->evbuf.as<double>();
+      PF_CUDA(cudaMemcpyAsync(Td, T.data(), (size_t)m * m * sizeof(double), cudaMemcpyHostToDevice, s));
+      PF_CHECK(syevd(c, Td, m, m, Td + (size_t)m * m));
+      std::vector<double> ev(m), y0(m), y1(m);
+      PF_CUDA(cudaMemcpyAsync(ev.data(), Td + (size_t)m * m, m * sizeof(double), cudaMemcpyDeviceToHost, s));
+      double last_lo = 0, last_hi = 0;
+      PF_CUDA(cudaMemcpyAsync(&last_lo, Td + (size_t)0 * m + (m - 1), sizeof(double), cudaMemcpyDeviceToHost, s));
+      PF_CUDA(cudaMemcpyAsync(&last_hi, Td + (size_t)(m - 1) * m + (m - 1), sizeof(double), cudaMemcpyDeviceToHost, s));
+      PF_CUDA(cudaStreamSynchronize(s));
+      lo = ev[0];
+      hi = ev[m - 1];
+      e_lo = std::fabs(beta * last_lo);
+      e_hi = std::fabs(beta * last_hi);
+      const double scale = std::max(std::fabs(lo), std::fabs(hi));
+      if ((e_lo <= 1e-12 * scale && e_hi <= 1e-12 * scale) || beta < 1e-300) break;
+    }
+    if (beta < 1e-300) break;
+    // v0 <- v1, v1 <- w / beta
+    std::swap(v0, v1);
+    PF_CHECK(D.axpbypcz(dim, 1.0 / beta, w, 0.0, v1, 0.0, nullptr, s));
+  }
+  *emin = lo;
+  *emax = hi;
+  *err = std::max(e_lo, e_hi);
+  return POLFED_OK;
+}
+
+int moments(polfed_ctx* c, HamPlan& plan, double* mean, double* var) {
+  cudaStream_t s = c->stream;
+  PF_CHECK(c->small.ensure(std::max(c->small.n, (size_t)64), &c->ws_total, c->ws_limit));
+  double* out = c->small.as<double>();
+  PF_CUDA(cudaMemsetAsync(out, 0, 3 * sizeof(double), s));
+  k_moments<<<std::min(plan.geo.n_groups + 0, 152 * 4), 256, 0, s>>>(plan.geo, plan.tab.U_lo, plan.tab.T_hi,
+                                                                      plan.tab.F_lo, plan.tab.F_hi, plan.tab.C_x, out);
+  PF_CUDA(cudaGetLastError());
+  count_launch();
+  double h[3];
+  PF_CUDA(cudaMemcpyAsync(h, out, sizeof(h), cudaMemcpyDeviceToHost, s));
+  PF_CUDA(cudaStreamSynchronize(s));
+  const double n = (double)plan.geo.dim;
+  *mean = h[0] / n;
+  *var = h[1] / n - (*mean) * (*mean) + h[2] / n;
+  return POLFED_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int polfed_ctx_create(int32_t device, size_t workspace_bytes, polfed_ctx** out) {
+  if (!out) return fail(POLFED_EINVAL, "out is NULL");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return fail(POLFED_EINVAL, "invalid CUDA device");
+  }
+  ScopedDevice sd(device);
+  polfed_ctx* c = new polfed_ctx();
+  c->device = device;
+  c->ws_limit = workspace_bytes;
+  polfed_opts_default(&c->opts);
+  memset(&c->last, 0, sizeof(c->last));
+  if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    delete c;
+    return fail(POLFED_ECUDA, "cudaStreamCreate failed");
+  }
+  c->own_stream = true;
+  if (cusolverDnCreate(&c->solver) != CUSOLVER_STATUS_SUCCESS) {
+    cudaStreamDestroy(c->stream);
+    delete c;
+    return fail(POLFED_ECUDA, "cusolverDnCreate failed");
+  }
+  cusolverDnSetStream(c->solver, c->stream);
+  *out = c;
+  return POLFED_OK;
+}
+
+void polfed_ctx_destroy(polfed_ctx* c) {
+  if (!c) return;
+  ScopedDevice sd(c->device);
+  cudaStreamSynchronize(c->stream);
+  c->basis.release();
+  c->U.release();
+  c->R.release();
+  c->fscr.release();
+  c->ritz.release();
+  c->small.release();
+  c->evbuf.release();
+  c->work.release();
+  c->vecs.release();
+  c->dense.release();
+  if (c->solver) cusolverDnDestroy(c->solver);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+int polfed_ctx_set_stream(polfed_ctx* c, polfed_stream_t stream) {
+  if (!c) return fail(POLFED_EINVAL, "ctx is NULL");
+  ScopedDevice sd(c->device);
+  if (c->own_stream && c->stream) {
+    cudaStreamSynchronize(c->stream);
+    cudaStreamDestroy(c->stream);
+  }
+  c->stream = (cudaStream_t)stream;
+  c->own_stream = false;
+  cusolverDnSetStream(c->solver, c->stream);
+  return POLFED_OK;
+}
+
+int polfed_block_lanczos(polfed_ctx* c, const polfed_model* model, double e_lo, double e_hi, double sigma, int32_t K,
+                         int32_t n_b, int32_t N_ev, double* d_evecs, double* evals, double* resid, int32_t* n_conv) {
+  if (!c) return fail(POLFED_EINVAL, "ctx is NULL");
+  if (!evals) return fail(POLFED_EINVAL, "evals is NULL");
+  if (!(e_lo < e_hi) || !std::isfinite(e_lo) || !std::isfinite(e_hi)) return fail(POLFED_EINVAL, "need e_lo < e_hi");
+  if (!(sigma > -1.0 && sigma < 1.0)) return fail(POLFED_EINVAL, "sigma must be in (-1, 1)");
+  if (K < 1 || K > 10000000) return fail(POLFED_EINVAL, "K must be in 1..1e7");
+  if (n_b < 1 || n_b > 128) return fail(POLFED_EINVAL, "n_b must be in 1..128");
+  ScopedDevice sd(c->device);
+  HamPlan plan;
+  PF_CHECK(plan.init(model, c->stream, false));
+  const double hn = std::max(std::fabs(e_lo), std::fabs(e_hi));
+  LanczosParams P{e_lo, e_hi, sigma, K, round_block(n_b), N_ev, c->opts, c->opts.tol_resid * hn / (0.5 * (e_hi - e_lo)),
+                  false};
+  LanczosOut o;
+  const double t0 = now_s();
+  int rc = run_lanczos(c, plan, P, d_evecs, o);
+  if (rc != POLFED_OK && rc != POLFED_ENOCONV) return rc;
+  const double half = 0.5 * (e_hi - e_lo), mid = 0.5 * (e_hi + e_lo);
+  for (int i = 0; i < o.n_out; i++) {
+    evals[i] = o.evals_t[i] * half + mid;
+    if (resid) resid[i] = o.resid_t[i] * half;
+  }
+  if (n_conv) *n_conv = o.n_out;
+  polfed_stats& st = c->last;
+  memset(&st, 0, sizeof(st));
+  st.K = K;
+  st.m = o.m;
+  st.n_b = P.S;
+  st.n_conv = o.n_conv;
+  st.n_ritz_checks = o.checks;
+  st.dim = plan.geo.dim;
+  st.matvec_cols = o.matvec_cols;
+  st.e_lo = e_lo;
+  st.e_hi = e_hi;
+  st.sigma = sigma;
+  st.t_filter = o.t_filter;
+  st.t_reorth = o.t_reorth;
+  st.t_qr = o.t_qr;
+  st.t_teig = o.t_teig;
+  st.t_ritz = o.t_ritz;
+  st.t_total = now_s() - t0;
+  st.status = rc;
+  for (int i = 0; i < o.n_out; i++) st.max_resid = std::max(st.max_resid, o.resid_t[i] * half);
+  return rc;
+}
+
+int polfed_eigs(polfed_ctx* c, const polfed_model* model, double eps_target, int32_t N_ev, int32_t K, int32_t n_b,
+                const polfed_opts* opts, double* evals, double* d_evecs, double* resid, polfed_stats* stats) {
+  if (!c) return fail(POLFED_EINVAL, "ctx is NULL");
+  if (!evals) return fail(POLFED_EINVAL, "evals is NULL");
+  if (!(eps_target >= 0.0 && eps_target <= 1.0)) return fail(POLFED_EINVAL, "eps_target must be in [0, 1]");
+  if (n_b < 1 || n_b > 128) return fail(POLFED_EINVAL, "n_b must be in 1..128");
+  if (K < 0 || K > 10000000) return fail(POLFED_EINVAL, "K must be in 0..1e7");
+  polfed_opts o;
+  if (opts)
+    o = *opts;
+  else
+    polfed_opts_default(&o);
+  if (!(o.p > 0.0 && o.p < 1.0)) return fail(POLFED_EINVAL, "opts.p must be in (0, 1)");
+  if (o.precision != POLFED_F64 && o.precision != POLFED_F32 && o.precision != POLFED_DF64)
+    return fail(POLFED_EINVAL, "bad opts.precision");
+  c->opts = o;
+  c->have_opts = true;
+  ScopedDevice sd(c->device);
+  const double t0 = now_s();
+  const Counters cn0 = counters();
+  HamPlan plan;
+  PF_CHECK(plan.init(model, c->stream, false));
+  count_launch(4);  // table kernels
+  const int64_t dim = plan.geo.dim;
+  if (N_ev < 1 || N_ev > dim) return fail(POLFED_EINVAL, "N_ev must be in 1..dim");
+  // 1. spectral bounds
+  double Emin = 0, Emax = 0, berr = 0;
+  int64_t mv = 0;
+  PF_CHECK(spectral_bounds(c, plan, o, &Emin, &Emax, &berr, &mv));
+  const double t_b = now_s() - t0;
+  if (!(Emax > Emin)) return fail(POLFED_EINVAL, "degenerate spectrum (E_max == E_min)");
+  const double width = Emax - Emin;
+  const double pad = 1e-6 * width + 10.0 * berr;
+  const double e_lo = Emin - pad, e_hi = Emax + pad;
+  const double Estar = Emin + eps_target * width;
+  double sigma = (2.0 * Estar - e_lo - e_hi) / (e_hi - e_lo);
+  if (std::fabs(sigma) < 1e-14) sigma = 0.0;
+  if (!(sigma > -1.0 && sigma < 1.0)) return fail(POLFED_EINVAL, "target outside the spectrum");
+  // 2. order K from the density of states at the target
+  double mean = 0, var = 0;
+  PF_CHECK(moments(c, plan, &mean, &var));
+  const double gam = std::sqrt(std::max(var, 1e-300));
+  const double rho = (double)dim / (std::sqrt(2.0 * M_PI) * gam) * std::exp(-0.5 * (Estar - mean) * (Estar - mean) / (gam * gam));
+  const double rho_t = rho * 0.5 * (e_hi - e_lo);
+  if (K == 0) {
+    const double y = lobe_root(o.p);
+    const double n_target = (1.0 + o.k_margin) * N_ev;
+    double k1 = 2.0 * y * std::sqrt(1.0 - sigma * sigma) * rho_t / n_target;  // K + 1
+    int k = (int)std::floor(k1 - 1.0);
+    if (sigma == 0.0) k &= ~1;
+    K = std::max(2, std::min(k, 10000000));
+  }
+  if (o.verbose || debug_on())
+    fprintf(stderr, "[polfed] dim %lld  E_min %.12f  E_max %.12f (err %.1e)  sigma %.3e  mean %.4f  Gamma %.4f  rho~ %.4e  K %d\n",
+            (long long)dim, Emin, Emax, berr, sigma, mean, gam, rho_t, K);
+  // 3. block Lanczos
+  const int S = round_block(n_b);
+  const double hnorm0 = std::max(std::fabs(Emin), std::fabs(Emax));
+  LanczosParams P{e_lo, e_hi, sigma, K, S, N_ev, o, o.tol_resid * hnorm0 / (0.5 * (e_hi - e_lo)), false};
+  LanczosOut lo;
+  int rc = run_lanczos(c, plan, P, d_evecs, lo);
+  if (rc != POLFED_OK && rc != POLFED_ENOCONV) return rc;
+  const double half = 0.5 * (e_hi - e_lo), mid = 0.5 * (e_hi + e_lo);
+  const double hnorm = std::max(std::fabs(Emin), std::fabs(Emax));
+  polfed_stats st;
+  memset(&st, 0, sizeof(st));
+  for (int i = 0; i < lo.n_out; i++) {
+    evals[i] = lo.evals_t[i] * half + mid;
+    const double r = lo.resid_t[i] * half;
+    if (resid) resid[i] = r;
+    st.max_resid = std::max(st.max_resid, r);
+  }
+  st.K = K;
+  st.m = lo.m;
+  st.n_b = S;
+  st.n_conv = lo.n_conv;
+  st.n_ritz_checks = lo.checks;
+  st.status = rc;
+  st.dim = dim;
+  st.matvec_cols = lo.matvec_cols + mv;
+  st.E_min = Emin;
+  st.E_max = Emax;
+  st.e_lo = e_lo;
+  st.e_hi = e_hi;
+  st.sigma = sigma;
+  st.target = Estar;
+  st.rho_sigma = rho_t;
+  st.t_bounds = t_b;
+  st.t_filter = lo.t_filter;
+  st.t_reorth = lo.t_reorth;
+  st.t_qr = lo.t_qr;
+  st.t_teig = lo.t_teig;
+  st.t_ritz = lo.t_ritz;
+  st.t_total = now_s() - t0;
+  const Counters cn1 = counters();
+  st.n_launches = cn1.launches - cn0.launches;
+  st.n_step_launches = cn1.step_launches - cn0.step_launches;
+  st.step_gpu_s = cn1.step_gpu_s - cn0.step_gpu_s;
+  st.step_alg_bytes = cn1.step_alg_bytes - cn0.step_alg_bytes;
+  c->last = st;
+  if (stats) *stats = st;
+  if (rc == POLFED_OK && st.max_resid > o.tol_resid * hnorm && o.verbose)
+    fprintf(stderr, "[polfed] warning: max residual %.3e exceeds tol %.3e\n", st.max_resid, o.tol_resid * hnorm);
+  return rc;
+}
+
+}  // extern "C"

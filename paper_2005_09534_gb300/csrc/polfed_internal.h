@@ -1,0 +1,159 @@
+// Internal declarations of the POLFED GB300 library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/polfed.h"
+
+namespace polfed {
+
+// ----------------------------------------------------------------- errors
+struct Error {
+  int code;
+  std::string msg;
+};
+void set_error(int code, const std::string& msg);
+int fail(int code, const std::string& msg);  // set_error + return code
+
+#define PF_CUDA(call)                                                                          \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess)                                                                     \
+      return ::polfed::fail(POLFED_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+#define PF_CHECK(call)          \
+  do {                          \
+    int rc_ = (call);           \
+    if (rc_ != POLFED_OK) return rc_; \
+  } while (0)
+
+// ------------------------------------------------------------- counters
+// Process-wide counters of kernel launches and of the step kernel's device
+// time (CUDA events on the launching stream); calls report their deltas.
+struct Counters {
+  int64_t launches = 0;
+  int64_t step_launches = 0;
+  double step_gpu_s = 0.0;
+  double step_alg_bytes = 0.0;
+};
+Counters& counters();
+inline void count_launch(int64_t n = 1) { counters().launches += n; }
+
+// -------------------------------------------------------------- binomials
+// C(n, k) for 0 <= n, k <= 32 (C(32,16) < 2^31).
+uint32_t binom_host(int n, int k);
+void upload_binomials();  // __constant__ table, once per device
+
+// ------------------------------------------------- Hamiltonian operator plan
+// A term of Eq. (1) between sites i < j with coupling class l (1: J1, 2: J2).
+struct Bond {
+  int i, j, cls;
+};
+
+constexpr int kMaxBonds = 64;
+constexpr int kMaxCross = 16;
+
+// Split of the L bits into a low part (bits 0..b-1) and a high part (bits
+// b..L-1).  Rows whose states share the high part s_hi form one contiguous
+// "group"; rank(s) = T_hi[s_hi] + T_lo[s_lo] (combinatorial number system).
+struct HamGeometry {
+  int L, b, nh, n_up, periodic;
+  int64_t dim;
+  double J1, J2, Delta;
+  double h[32];
+  // literal terms of Eq. (1), classified by where their two sites lie
+  int n_low1, n_low2;    // low bonds, class 1 first then class 2
+  uint32_t low_mask[kMaxBonds];
+  int n_high1, n_high2;  // high bonds (masks relative to bit b)
+  uint32_t high_mask[kMaxBonds];
+  int n_cross;           // one site in each part
+  int cross_lo[kMaxCross], cross_hi[kMaxCross], cross_cls[kMaxCross];
+  int cls_off[34];       // offset of popcount class c in the U_lo table
+  int max_group;         // largest group (rows)
+  int n_groups;          // valid groups
+  int rec_stride;        // uint16 entries per neighbour record (16 or 32)
+};
+
+// Device tables of a geometry (owned by HamPlan).
+struct HamTables {
+  uint16_t* T_lo;   // [2^b] rank of s_lo among b-bit strings of equal popcount
+  uint16_t* U_lo;   // [2^b] inverse: U_lo[cls_off[c] + k] = k-th b-bit string with popcount c
+  int32_t* T_hi;    // [2^nh] first row of group s_hi, -1 if the group is empty
+  int32_t* order;   // [n_groups] groups, largest first
+  double* F_lo;     // [2^b] diagonal part from low bonds and low fields (H units)
+  double* F_hi;     // [2^nh] diagonal part from high bonds and high fields
+  double* C_x;      // [2^n_cross] diagonal part from cross bonds by "differ" pattern
+  // [2^b * rec_stride] per-row neighbour record, indexed by cls_off[c] + local index:
+  //   entry 0: s_lo; entries 1..: local index of each low-bond neighbour (0xFFFF if the
+  //   pair is parallel); last entries (from the end): local index, in the neighbouring
+  //   popcount class, of s_lo with the low site of cross bond k flipped
+  uint16_t* rec;
+};
+
+int build_geometry(const polfed_model* m, int b_override, HamGeometry* g);
+
+class HamPlan {
+ public:
+  HamGeometry geo;
+  HamTables tab{};
+  void* dev = nullptr;       // one allocation for all tables
+  // per-precision alpha/beta-scaled tables (F_lo, F_hi, C_x), indexed by dtype
+  void* typed[3] = {nullptr, nullptr, nullptr};
+  size_t typed_bytes[3] = {0, 0, 0};
+  bool typed_ok[3] = {false, false, false};
+  double typed_lo[3] = {0, 0, 0}, typed_hi[3] = {0, 0, 0};
+  cudaStream_t stream = nullptr;
+  bool stream_alloc = false;  // tables from cudaMallocAsync
+
+  int init(const polfed_model* m, cudaStream_t s, bool stream_ordered, int b_override = -1);
+  int prepare_typed(int kind, double e_lo, double e_hi);  // alpha/beta-scaled tables
+  void release();
+  ~HamPlan() { release(); }
+};
+
+// Arguments of one H~-slice kernel launch: out = cX*X + cH*(H~ b1) + cB*b2, all
+// operands slice-major (ld = W elements, W = VEC * LPR).
+struct StepArgs {
+  const void* b1;
+  const void* b2;  // may be null when cB == 0
+  const void* x;   // may be null when cX == 0
+  void* out;
+  double cX, cH, cB;
+  int lpr;         // lanes per row: slice = 16 * lpr bytes
+};
+
+// Launch one step (kind = POLFED_F32 / F64 / DF64 storage type).
+int launch_ham_step(const HamPlan& plan, int kind, const StepArgs& a, cudaStream_t s);
+
+// Elements per slice for a precision and lanes-per-row.
+int slice_width(int kind, int lpr);
+size_t elem_bytes(int kind);  // internal storage element size (DF64: 8 = two floats)
+
+// Filter engine over an arbitrary-width ABI block.  in/out are row-major
+// dim x n_b of "abi_kind" (POLFED_F32: float, else double).
+struct FilterScratch {
+  void* xs = nullptr;  // slice buffers (dim x W each)
+  void* ba = nullptr;
+  void* bb = nullptr;
+  float* flag = nullptr;  // [4] max |x|, max |y| (as float bits)
+  size_t bytes = 0;
+};
+int filter_block(HamPlan& plan, int kind, const double* coeffs, int K, double invD, const void* in, void* out,
+                 int n_b, int abi_kind, FilterScratch& scr, cudaStream_t s, int lpr_hint = 0);
+int apply_block(HamPlan& plan, int kind, const void* in, void* out, int n_b, int abi_kind, FilterScratch& scr,
+                cudaStream_t s, int lpr_hint = 0);
+size_t filter_scratch_bytes(const HamPlan& plan, int kind, int lpr);
+int choose_lpr(int kind, int n_b);
+
+// Chebyshev coefficients of Eq. (2) in FP64: c_n, n = 0..K, and D.
+void cheb_coeffs(double sigma, int K, std::vector<double>& c, double& D);
+
+// Basis kernel (polfed_basis_build).
+int launch_basis(int L, int n_up, uint32_t* d_states, int64_t dim, cudaStream_t s);
+
+}  // namespace polfed
