@@ -70,10 +70,10 @@ void upload_binomials() {
 // -------------------------------------------------------------- geometry
 static int choose_b(int L) {
   // >= 2^10 groups at large L (load balance over 152 SMs) and a 128-byte-row
-  // group tile of C(11,5) * 128 B = 59 KB (three CTAs per SM)
+  // group block of at most C(10,5) * 128 B = 32 KB
   int b = L - 10;
   if (const char* e = getenv("POLFED_LOWBITS")) b = atoi(e);
-  if (b > 11) b = 11;
+  if (b > 10) b = 10;
   if (b < 2) b = 2;
   if (L - b < 2) b = L - 2;
   return b;
@@ -150,7 +150,8 @@ int build_geometry(const polfed_model* m, int b_override, HamGeometry* g) {
     const bool j2 = g->n_low2 + g->n_high2 > 0 || m->J2 != 0.0;
     const int maxcr = j2 ? 6 : 2;
     g->rec_stride = j2 ? 32 : 16;
-    if (1 + g->n_low1 + g->n_low2 + maxcr > g->rec_stride) return fail(POLFED_EINVAL, "too many low bonds for the record");
+    if (2 + g->n_low1 + g->n_low2 + maxcr > g->rec_stride) return fail(POLFED_EINVAL, "too many low bonds for the record");
+    if (g->n_high1 + g->n_high2 > kMaxHigh) return fail(POLFED_EINVAL, "too many high bonds for the group table");
   }
   g->max_group = 0;
   g->n_groups = 0;
@@ -188,14 +189,61 @@ __global__ void k_tables_rec(const HamGeometry g, const uint16_t* T_lo, uint16_t
   if (a >= (1 << g.b)) return;
   const int RS = g.rec_stride;
   uint16_t* r = rec + (size_t)(g.cls_off[__popc(a)] + T_lo[a]) * RS;
-  for (int e = 0; e < RS; e++) r[e] = 0xFFFF;
+  for (int e = 0; e < RS; e++) r[e] = 0;
   r[0] = (uint16_t)a;
-  const int nl = g.n_low1 + g.n_low2;
-  for (int k = 0; k < nl; k++) {
+  int n1 = 0, n2 = 0;
+  for (int k = 0; k < g.n_low1; k++) {
     const uint32_t m = g.low_mask[k];
-    if (__popc((uint32_t)a & m) == 1) r[1 + k] = T_lo[a ^ m];
+    if (__popc((uint32_t)a & m) == 1) r[2 + n1++] = T_lo[a ^ m];
   }
+  for (int k = g.n_low1; k < g.n_low1 + g.n_low2; k++) {
+    const uint32_t m = g.low_mask[k];
+    if (__popc((uint32_t)a & m) == 1) r[2 + n1 + n2++] = T_lo[a ^ m];
+  }
+  r[1] = (uint16_t)(n1 | (n2 << 8));
   for (int k = 0; k < g.n_cross; k++) r[RS - 1 - k] = T_lo[a ^ (1 << g.cross_lo[k])];
+}
+
+// Per-group constants in schedule order.
+__global__ void k_tables_groups(const HamGeometry g, const int32_t* T_hi, const int32_t* order, GroupRec* gr) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= g.n_groups) return;
+  const int grp = order[idx];
+  GroupRec r;
+  const int n_lo = g.n_up - __popc(grp);
+  r.r0 = T_hi[grp];
+  r.n_g = (int)c_binom[g.b][n_lo];
+  r.cls_base = g.cls_off[n_lo];
+  int cnt = 0, cnt1 = 0;
+  for (int k = 0; k < g.n_high1 + g.n_high2; k++) {
+    const uint32_t m = g.high_mask[k];
+    if (__popc((uint32_t)grp & m) == 1 && cnt < kMaxHigh) {
+      r.hn_base[cnt++] = T_hi[grp ^ m];
+      if (k < g.n_high1) cnt1++;
+    }
+  }
+  for (int k = cnt; k < kMaxHigh; k++) r.hn_base[k] = 0;
+  r.n_hn = cnt;
+  r.n_hn1 = cnt1;
+  int need = 0;
+  for (int k = 0; k < 8; k++) {
+    r.cr_base[k] = 0;
+    r.cr_n[k] = 0;
+    if (k < g.n_cross) {
+      const int hb = (grp >> g.cross_hi[k]) & 1;
+      if (!hb) need |= 1 << k;  // the low bit must differ from the high bit
+      const int g2 = grp ^ (1 << g.cross_hi[k]);
+      const int n_lo2 = g.n_up - __popc(g2);
+      // rows with the bond antiparallel exist only if the neighbouring class is valid
+      if (T_hi[g2] >= 0 && n_lo2 >= 0 && n_lo2 <= g.b) {
+        r.cr_base[k] = T_hi[g2];
+        r.cr_n[k] = (int)c_binom[g.b][n_lo2];
+      }
+    }
+  }
+  r.need_mask = need;
+  r.pad0 = r.pad1 = 0;
+  gr[idx] = r;
 }
 
 __global__ void k_tables_hi(const HamGeometry g, int32_t* T_hi, double* F_hi) {
@@ -242,6 +290,7 @@ struct KCd {
 };
 struct KCdf {
   float2 cX, cH, cB, o1, o2;
+  int exact;  // cX, cH, cB are 0 or +-2^k: multiply hi and lo separately (exact)
 };
 
 // Float-float arithmetic: a value is hi + lo with |lo| <= ulp(hi)/2.
@@ -327,6 +376,12 @@ struct NDF {
                                               bool j2) {
     float2 y = df_add(df_mul(ad, x1), df_mul(k.o1, fast_two_sum(a1.x, a1.y)));
     if (j2) y = df_add(y, df_mul(k.o2, fast_two_sum(a2.x, a2.y)));
+    if (k.exact) {
+      float2 r = make_float2(k.cH.x * y.x, k.cH.x * y.y);
+      if (hx) r = df_add(r, make_float2(k.cX.x * xv.x, k.cX.x * xv.y));
+      if (hb) r = df_add(r, make_float2(k.cB.x * b2v.x, k.cB.x * b2v.y));
+      return r;
+    }
     float2 r = df_mul(k.cH, y);
     if (hx) r = df_add(r, df_mul(k.cX, xv));
     if (hb) r = df_add(r, df_mul(k.cB, b2v));
@@ -342,238 +397,600 @@ union V16 {
 };
 
 // ---------------------------------------------------------- the step kernel
-struct GroupInfo {
-  int r0, n_g, cls_base, n_hn1, n_hn;
-  int hn_base[kMaxBonds];
-  int cr_base[8], cr_need[8];
-};
-
 struct StepTables {
   const uint16_t* rec;
-  const int32_t* T_hi;
-  const int32_t* order;
+  const GroupRec* grec;
   const void* F_lo;  // typed, alpha-scaled
-  const void* F_hi;  // typed, alpha-scaled, includes -alpha*beta
+  const void* F_hi;  // typed, alpha-scaled, includes -alpha*beta (indexed by s_hi)
   const void* C_x;   // typed, alpha-scaled
+  const int32_t* order;
 };
 
+// One Clenshaw / H~ step on a 16*LPR-byte column slice:
+//   out = cX * x + cH * (H~ b1) + cB * b2     (row-major slice buffers, ld = W)
+// A CTA takes groups in schedule order; a group's rows of b1 are staged in
+// shared memory, then rows are processed in passes of PCH rows per thread:
+//   H: whole neighbouring-group blocks (high bonds) streamed with coalesced loads,
+//   L: low-bond neighbours gathered from the staged rows (compact per-row record),
+//   C: cross-bond neighbours gathered from global memory,
+//   F: diagonal, combination with x and b2, store.
 template <class NT, int LPR, bool J2>
-__global__ void __launch_bounds__(256) k_ham_step(const HamGeometry g, const StepTables t,
-                                                   const typename NT::S* __restrict__ b1,
-                                                   const typename NT::S* b2, const typename NT::S* __restrict__ x,
-                                                   typename NT::S* out, const typename NT::KC kc, int has_x,
-                                                   int has_b2) {
+__global__ void __launch_bounds__(256, 2) k_ham_step(const HamGeometry g, const StepTables t,
+                                                      const typename NT::S* __restrict__ b1,
+                                                      const typename NT::S* b2, const typename NT::S* __restrict__ x,
+                                                      typename NT::S* out, const typename NT::KC kc, int has_x,
+                                                      int has_b2) {
   using S = typename NT::S;
   using C = typename NT::C;
   using A = typename NT::A;
   constexpr int VEC = 16 / sizeof(S);
   constexpr int W = VEC * LPR;
   constexpr int MAXCR = J2 ? 6 : 2;  // cross bonds: (b-1,b), (L-1,0) and, with J2, four more
-  constexpr int HCH = 8;             // high-bond loads issued together per row
   constexpr int RS = J2 ? 32 : 16;   // record entries
-  constexpr int LOWMAX = RS - 1 - MAXCR;
-  constexpr int LCH = 4;             // low-bond shared-memory gathers batched together
+  constexpr int LOWMAX = RS - 2 - MAXCR;
+  constexpr int PCH = J2 ? 2 : 4;    // rows per thread per pass
+  constexpr int NT_ = 256;
+  constexpr int RSTEP = NT_ / LPR;   // rows between a thread's consecutive rows in a pass
 
   extern __shared__ __align__(16) unsigned char smem[];
   const int nlo_tab = 1 << g.b;
   S* tile = reinterpret_cast<S*>(smem);
   C* sFlo = reinterpret_cast<C*>(smem + (size_t)g.max_group * W * sizeof(S));
   C* sCx = sFlo + nlo_tab;
-  __shared__ GroupInfo gi;
-  __shared__ C s_fhi;
 
   const C* gFlo = reinterpret_cast<const C*>(t.F_lo);
   const C* gFhi = reinterpret_cast<const C*>(t.F_hi);
   const C* gCx = reinterpret_cast<const C*>(t.C_x);
-  for (int i = threadIdx.x; i < nlo_tab; i += blockDim.x) sFlo[i] = gFlo[i];
-  for (int i = threadIdx.x; i < (1 << g.n_cross); i += blockDim.x) sCx[i] = gCx[i];
+  for (int i = threadIdx.x; i < nlo_tab; i += NT_) sFlo[i] = gFlo[i];
+  for (int i = threadIdx.x; i < (1 << g.n_cross); i += NT_) sCx[i] = gCx[i];
 
-  const int warp = threadIdx.x >> 5, lane32 = threadIdx.x & 31;
-  const int unit = threadIdx.x / LPR, lane = threadIdx.x % LPR, units = blockDim.x / LPR;
-  const int n_cr = g.n_cross;
-  const int nlow = g.n_low1 + (J2 ? g.n_low2 : 0), nlow1 = g.n_low1;
+  const int tr = threadIdx.x / LPR, lane = threadIdx.x % LPR;
   int cr_lb[MAXCR], cr_c2[MAXCR];
 #pragma unroll
   for (int k = 0; k < MAXCR; k++) {
-    cr_lb[k] = k < n_cr ? g.cross_lo[k] : 0;
-    cr_c2[k] = k < n_cr && g.cross_cls[k] == 2;
+    cr_lb[k] = k < g.n_cross ? g.cross_lo[k] : 0;
+    cr_c2[k] = k < g.n_cross && g.cross_cls[k] == 2;
   }
 
   for (int gidx = blockIdx.x; gidx < g.n_groups; gidx += gridDim.x) {
-    const int grp = t.order[gidx];
+    const GroupRec* G = t.grec + gidx;
+    const int r0 = __ldg(&G->r0), n_g = __ldg(&G->n_g), cls_base = __ldg(&G->cls_base);
+    const int n_hn = __ldg(&G->n_hn), n_hn1 = __ldg(&G->n_hn1), need = __ldg(&G->need_mask);
+    int cr_bs[MAXCR];
+#pragma unroll
+    for (int k = 0; k < MAXCR; k++) cr_bs[k] = __ldg(&G->cr_base[k]);
+    const C fhi = gFhi[t.order[gidx]];
     __syncthreads();  // tables loaded / previous tile fully consumed
-    if (warp == 0) {
-      // high-bond neighbour groups (class-1 bonds listed first)
-      const int nhb = g.n_high1 + g.n_high2;
-      int cnt = 0, cnt1 = 0;
-      for (int k0 = 0; k0 < nhb; k0 += 32) {
-        const int k = k0 + lane32;
-        bool act = false;
-        int base = 0;
-        if (k < nhb) {
-          const uint32_t m = g.high_mask[k];
-          act = __popc((uint32_t)grp & m) == 1;
-          if (act) base = t.T_hi[grp ^ m];
-        }
-        const unsigned bal = __ballot_sync(0xffffffffu, act);
-        if (act) gi.hn_base[cnt + __popc(bal & ((1u << lane32) - 1u))] = base;
-        const unsigned m1 = (k0 + 32 <= g.n_high1) ? 0xffffffffu
-                            : (k0 >= g.n_high1)   ? 0u
-                                                  : ((1u << (g.n_high1 - k0)) - 1u);
-        cnt1 += __popc(bal & m1);
-        cnt += __popc(bal);
-      }
-      if (lane32 < n_cr) {
-        const int k = lane32;
-        gi.cr_need[k] = 1 - ((grp >> g.cross_hi[k]) & 1);  // the low bit must differ from the high bit
-        gi.cr_base[k] = t.T_hi[grp ^ (1 << g.cross_hi[k])];
-      }
-      if (lane32 == 0) {
-        const int n_lo = g.n_up - __popc(grp);
-        gi.r0 = t.T_hi[grp];
-        gi.n_g = (int)c_binom[g.b][n_lo];
-        gi.cls_base = g.cls_off[n_lo];
-        gi.n_hn1 = cnt1;
-        gi.n_hn = cnt;
-        s_fhi = gFhi[grp];
-      }
-    }
-    __syncthreads();
-    const int r0 = gi.r0, n_g = gi.n_g;
-    // stage the group's rows of b1 (contiguous: n_g * W elements)
     {
       const int4* src = reinterpret_cast<const int4*>(b1 + (size_t)r0 * W);
       int4* dst = reinterpret_cast<int4*>(tile);
       const int nchunk = n_g * LPR;
-      for (int c = threadIdx.x; c < nchunk; c += blockDim.x) dst[c] = __ldg(src + c);
+      for (int c = threadIdx.x; c < nchunk; c += NT_) dst[c] = __ldg(src + c);
     }
-    // group constants in registers (read once, not per row)
-    const int n_hn = gi.n_hn, n_hn1 = gi.n_hn1, cls_base = gi.cls_base;
-    int hb[HCH];
-#pragma unroll
-    for (int k = 0; k < HCH; k++) hb[k] = gi.hn_base[k];
-    int cr_nd[MAXCR], cr_bs[MAXCR];
-#pragma unroll
-    for (int k = 0; k < MAXCR; k++) {
-      cr_nd[k] = k < n_cr ? gi.cr_need[k] : 2;  // 2 never matches a bit
-      cr_bs[k] = k < n_cr ? gi.cr_base[k] : 0;
-    }
-    const C fhi = s_fhi;
     __syncthreads();
-    for (int loc = unit; loc < n_g; loc += units) {
-      // neighbour record of this row (shared by all groups of its class)
-      uint32_t rw[RS / 2];
-      {
-        const uint4* rp = reinterpret_cast<const uint4*>(t.rec + (size_t)(cls_base + loc) * RS);
+    for (int p0 = 0; p0 < n_g; p0 += RSTEP * PCH) {
+      A a1[PCH][VEC], a2[PCH][VEC];
 #pragma unroll
-        for (int q = 0; q < RS / 8; q++) {
-          const uint4 v = __ldg(rp + q);
-          rw[4 * q] = v.x;
-          rw[4 * q + 1] = v.y;
-          rw[4 * q + 2] = v.z;
-          rw[4 * q + 3] = v.w;
+      for (int i = 0; i < PCH; i++)
+#pragma unroll
+        for (int v = 0; v < VEC; v++) {
+          a1[i][v] = NT::zero();
+          a2[i][v] = NT::zero();
         }
-      }
-#define PF_ENTRY(e) ((rw[(e) >> 1] >> (((e)&1) * 16)) & 0xFFFFu)
-      const uint32_t s_lo = PF_ENTRY(0);
-      const size_t off = (size_t)(r0 + loc) * W + lane * VEC;
-      // 1. issue every independent global load of this row first
-      V16<S> xv, bv;
-      if (has_x) xv.i = __ldcs(reinterpret_cast<const int4*>(x + off));
-      if (has_b2) bv.i = __ldcs(reinterpret_cast<const int4*>(b2 + off));
-      V16<S> hv[HCH];
+      // ---- H: high-bond neighbours: the same local rows of another group;
+      //      loads of HU neighbours x PCH rows are issued before any is consumed
+      constexpr int HU = 2;
+      for (int k0 = 0; k0 < n_hn; k0 += HU) {
+        V16<S> u[HU][PCH];
 #pragma unroll
-      for (int k = 0; k < HCH; k++)
-        if (k < n_hn) hv[k].i = __ldg(reinterpret_cast<const int4*>(b1 + (size_t)(hb[k] + loc) * W + lane * VEC));
-      V16<S> cv[MAXCR];
-      uint32_t pattern = 0;
+        for (int j = 0; j < HU; j++) {
+          if (k0 + j < n_hn) {
+            const int base = __ldg(&G->hn_base[k0 + j]);
 #pragma unroll
-      for (int k = 0; k < MAXCR; k++) {
-        if ((int)((s_lo >> cr_lb[k]) & 1u) == cr_nd[k]) {
-          pattern |= 1u << k;
-          cv[k].i = __ldg(reinterpret_cast<const int4*>(b1 + (size_t)(cr_bs[k] + PF_ENTRY(RS - 1 - k)) * W + lane * VEC));
-        }
-      }
-      // 2. low bonds from shared memory while those loads are in flight
-      A a1[VEC], a2[VEC];
-#pragma unroll
-      for (int v = 0; v < VEC; v++) {
-        a1[v] = NT::zero();
-        a2[v] = NT::zero();
-      }
-#pragma unroll
-      for (int k0 = 0; k0 < LOWMAX; k0 += LCH) {
-        if (k0 < nlow) {
-          V16<S> u[LCH];
-          bool act[LCH];
-#pragma unroll
-          for (int i = 0; i < LCH; i++) {
-            const int k = k0 + i;
-            const uint32_t j = (k < LOWMAX) ? PF_ENTRY(1 + k) : 0xFFFFu;
-            act[i] = (k < nlow) && j != 0xFFFFu;
-            if (act[i]) u[i].i = *reinterpret_cast<const int4*>(tile + (size_t)j * W + lane * VEC);
+            for (int i = 0; i < PCH; i++) {
+              const int row = p0 + tr + RSTEP * i;
+              if (row < n_g)
+                u[j][i].i = __ldg(reinterpret_cast<const int4*>(b1 + (size_t)(base + row) * W + lane * VEC));
+            }
           }
+        }
 #pragma unroll
-          for (int i = 0; i < LCH; i++) {
-            if (act[i]) {
-              if (!J2 || k0 + i < nlow1) {
+        for (int j = 0; j < HU; j++) {
+          if (k0 + j < n_hn) {
+            const bool c1 = !J2 || k0 + j < n_hn1;
 #pragma unroll
-                for (int v = 0; v < VEC; v++) NT::acc(a1[v], u[i].s[v]);
-              } else {
+            for (int i = 0; i < PCH; i++) {
+              const int row = p0 + tr + RSTEP * i;
+              if (row < n_g) {
+                if (c1) {
 #pragma unroll
-                for (int v = 0; v < VEC; v++) NT::acc(a2[v], u[i].s[v]);
+                  for (int v = 0; v < VEC; v++) NT::acc(a1[i][v], u[j][i].s[v]);
+                } else {
+#pragma unroll
+                  for (int v = 0; v < VEC; v++) NT::acc(a2[i][v], u[j][i].s[v]);
+                }
               }
             }
           }
         }
       }
+      // ---- L + C: low bonds (shared memory) and cross bonds (global), LR rows at a time:
+      //      records of all LR rows first, then their cross-bond loads, then the gathers
+      constexpr int LR = J2 ? 1 : 2;
+      uint32_t key[PCH];  // s_lo | cross pattern << 16
+#pragma unroll
+      for (int i0 = 0; i0 < PCH; i0 += LR) {
+        uint32_t rw[LR][RS / 2];
+#pragma unroll
+        for (int j = 0; j < LR; j++) {
+          const int row = p0 + tr + RSTEP * (i0 + j);
+          const uint4* rp = reinterpret_cast<const uint4*>(t.rec + (size_t)(cls_base + (row < n_g ? row : 0)) * RS);
+#pragma unroll
+          for (int q = 0; q < RS / 8; q++) {
+            const uint4 v = __ldg(rp + q);
+            rw[j][4 * q] = v.x;
+            rw[j][4 * q + 1] = v.y;
+            rw[j][4 * q + 2] = v.z;
+            rw[j][4 * q + 3] = v.w;
+          }
+        }
+#define PF_ENTRY(j, e) ((rw[j][(e) >> 1] >> (((e)&1) * 16)) & 0xFFFFu)
+        V16<S> cv[LR][MAXCR];
+        uint32_t pat[LR];
+#pragma unroll
+        for (int j = 0; j < LR; j++) {
+          const int row = p0 + tr + RSTEP * (i0 + j);
+          const uint32_t s_lo = PF_ENTRY(j, 0);
+          pat[j] = 0;
+#pragma unroll
+          for (int k = 0; k < MAXCR; k++) {
+            if (row < n_g && k < g.n_cross && ((s_lo >> cr_lb[k]) & 1u) == ((need >> k) & 1)) {
+              pat[j] |= 1u << k;
+              cv[j][k].i = __ldg(
+                  reinterpret_cast<const int4*>(b1 + (size_t)(cr_bs[k] + PF_ENTRY(j, RS - 1 - k)) * W + lane * VEC));
+            }
+          }
+          key[i0 + j] = s_lo | (pat[j] << 16);
+        }
+#pragma unroll
+        for (int j = 0; j < LR; j++) {
+          const int i = i0 + j;
+          const int row = p0 + tr + RSTEP * i;
+          const uint32_t cnt = PF_ENTRY(j, 1);
+          const int n1 = row < n_g ? (int)(cnt & 0xFF) : 0;
+          const int nl = row < n_g ? n1 + (J2 ? (int)(cnt >> 8) : 0) : 0;
+          const int nmax = __reduce_max_sync(0xffffffffu, nl);
+#pragma unroll
+          for (int k0 = 0; k0 < LOWMAX; k0 += 4) {
+            if (k0 >= nmax) break;
+            V16<S> u[4];
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+              const int k = k0 + q;
+              if (k < LOWMAX && k < nl)
+                u[q].i = *reinterpret_cast<const int4*>(tile + (size_t)PF_ENTRY(j, 2 + k) * W + lane * VEC);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+              const int k = k0 + q;
+              if (k < LOWMAX && k < nl) {
+                if (!J2 || k < n1) {
+#pragma unroll
+                  for (int v = 0; v < VEC; v++) NT::acc(a1[i][v], u[q].s[v]);
+                } else {
+#pragma unroll
+                  for (int v = 0; v < VEC; v++) NT::acc(a2[i][v], u[q].s[v]);
+                }
+              }
+            }
+          }
+#pragma unroll
+          for (int k = 0; k < MAXCR; k++) {
+            if ((pat[j] >> k) & 1u) {
+              if (!J2 || !cr_c2[k]) {
+#pragma unroll
+                for (int v = 0; v < VEC; v++) NT::acc(a1[i][v], cv[j][k].s[v]);
+              } else {
+#pragma unroll
+                for (int v = 0; v < VEC; v++) NT::acc(a2[i][v], cv[j][k].s[v]);
+              }
+            }
+          }
+        }
 #undef PF_ENTRY
-      // 3. consume the high-bond and cross-bond loads
+      }
+      // ---- F: diagonal, combination, store (x and b2 loads issued per chunk of rows)
+      constexpr int FCH = 2;
 #pragma unroll
-      for (int k = 0; k < HCH; k++) {
-        if (k < n_hn) {
-          if (!J2 || k < n_hn1) {
+      for (int i0 = 0; i0 < PCH; i0 += FCH) {
+        V16<S> xv[FCH], bv[FCH];
 #pragma unroll
-            for (int v = 0; v < VEC; v++) NT::acc(a1[v], hv[k].s[v]);
-          } else {
+        for (int j = 0; j < FCH; j++) {
+          const int row = p0 + tr + RSTEP * (i0 + j);
+          if (row < n_g) {
+            const size_t off = (size_t)(r0 + row) * W + lane * VEC;
+            if (has_x) xv[j].i = __ldcs(reinterpret_cast<const int4*>(x + off));
+            if (has_b2) bv[j].i = __ldcs(reinterpret_cast<const int4*>(b2 + off));
+          }
+        }
 #pragma unroll
-            for (int v = 0; v < VEC; v++) NT::acc(a2[v], hv[k].s[v]);
+        for (int j = 0; j < FCH; j++) {
+          const int i = i0 + j;
+          const int row = p0 + tr + RSTEP * i;
+          if (row < n_g) {
+            const size_t off = (size_t)(r0 + row) * W + lane * VEC;
+            const uint32_t s_lo = key[i] & 0xFFFFu, pattern = key[i] >> 16;
+            const C ad = NT::add3(sFlo[s_lo], fhi, sCx[pattern]);
+            V16<S> xo, res;
+            xo.i = *reinterpret_cast<const int4*>(tile + (size_t)row * W + lane * VEC);
+#pragma unroll
+            for (int v = 0; v < VEC; v++)
+              res.s[v] = NT::combine(has_x ? xv[j].s[v] : S(), xo.s[v], has_b2 ? bv[j].s[v] : S(), a1[i][v],
+                                     a2[i][v], ad, kc, has_x, has_b2, J2);
+            __stcg(reinterpret_cast<int4*>(out + off), res.i);
           }
         }
       }
-      for (int k = HCH; k < n_hn; k++) {  // rare: more than HCH active high bonds
-        V16<S> u;
-        u.i = __ldg(reinterpret_cast<const int4*>(b1 + (size_t)(gi.hn_base[k] + loc) * W + lane * VEC));
-        if (!J2 || k < n_hn1) {
-#pragma unroll
-          for (int v = 0; v < VEC; v++) NT::acc(a1[v], u.s[v]);
-        } else {
-#pragma unroll
-          for (int v = 0; v < VEC; v++) NT::acc(a2[v], u.s[v]);
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < MAXCR; k++) {
-        if ((pattern >> k) & 1u) {
-          if (!J2 || !cr_c2[k]) {
-#pragma unroll
-            for (int v = 0; v < VEC; v++) NT::acc(a1[v], cv[k].s[v]);
-          } else {
-#pragma unroll
-            for (int v = 0; v < VEC; v++) NT::acc(a2[v], cv[k].s[v]);
-          }
-        }
-      }
-      const C ad = NT::add3(sFlo[s_lo], fhi, sCx[pattern]);
-      V16<S> xo, res;
-      xo.i = *reinterpret_cast<const int4*>(tile + (size_t)loc * W + lane * VEC);
-#pragma unroll
-      for (int v = 0; v < VEC; v++)
-        res.s[v] = NT::combine(has_x ? xv.s[v] : S(), xo.s[v], has_b2 ? bv.s[v] : S(), a1[v], a2[v], ad, kc,
-                               has_x, has_b2, J2);
-      __stcg(reinterpret_cast<int4*>(out + off), res.i);
     }
   }
+}
+
+// ------------------------------------------------- TMA-pipelined step kernel
+// The same step for 128-byte slices with whole groups moved by the bulk-copy
+// (TMA) engine: a persistent CTA per SM takes groups in schedule order; the
+// group's own rows of b1 are fetched into a double-buffered shared tile, and
+// the neighbouring groups' blocks reached through high bonds stream through a
+// NSTAGE-deep shared ring (mbarrier completion, bounded waits).  Each thread
+// owns up to RPT rows (8 lanes of 16 bytes per row); x and b2 rows are loaded
+// into registers when the group starts and consumed at the end.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: false if the phase did not complete within the iteration cap
+// or another thread already gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag) {
+  for (uint32_t it = 0; it < (1u << 22); ++it) {
+    if (mbar_try_wait(b, parity)) return true;
+    if (*abort_flag) return false;
+  }
+  return false;
+}
+
+constexpr int kTmaConsumerWarps = 16;
+constexpr int kTmaThreads = 32 * (kTmaConsumerWarps + 1);  // warp 0 issues the copies
+constexpr int kTmaRowsPerThread = 2;  // 128 row units x 2 = 256 rows >= C(10,5) = 252
+__host__ __device__ constexpr int tma_stages(bool j2) { return j2 ? 2 : 3; }
+
+template <class NT, bool J2>
+__global__ void __launch_bounds__(kTmaThreads, 1)
+    k_ham_step_tma(const HamGeometry g, const StepTables t, const typename NT::S* __restrict__ b1,
+                   const typename NT::S* b2, const typename NT::S* __restrict__ x, typename NT::S* out,
+                   const typename NT::KC kc, int has_x, int has_b2, int* err) {
+  using S = typename NT::S;
+  using C = typename NT::C;
+  using A = typename NT::A;
+  constexpr int LPR = 4;             // lanes per 128-byte row
+  constexpr int VEC = 16 / sizeof(S);  // elements per 16-byte chunk
+  constexpr int W = 2 * VEC * LPR;     // elements per row (two chunks per lane)
+  constexpr int VL = 2 * VEC;          // elements per lane
+  constexpr int MAXCR = J2 ? 6 : 2;
+  constexpr int RS = J2 ? 32 : 16;
+  constexpr int LOWMAX = RS - 2 - MAXCR;
+  constexpr int NS = tma_stages(J2);
+  constexpr int RPT = kTmaRowsPerThread;
+  constexpr int UNITS = 32 * kTmaConsumerWarps / LPR;
+
+  extern __shared__ __align__(128) unsigned char smem[];
+  const size_t stg = (size_t)g.max_group * W;  // elements per stage
+  S* own = reinterpret_cast<S*>(smem);         // [2][stg]
+  S* ring = own + 2 * stg;                     // [NS][stg]
+  uint16_t* sRec = reinterpret_cast<uint16_t*>(ring + NS * stg);  // [2^b][RS] neighbour records
+  C* sFlo = reinterpret_cast<C*>(sRec + ((size_t)RS << g.b));
+  C* sCx = sFlo + (1 << g.b);
+  __shared__ __align__(8) uint64_t own_full[2], own_empty[2], full[NS], empty[NS];
+  __shared__ __align__(16) GroupRec s_grp[2];  // constants of the group in each own buffer
+  __shared__ int s_abort;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane32 = tid & 31;
+  if (tid == 0) {
+    for (int i = 0; i < 2; i++) {
+      mbar_init(&own_full[i], 1);
+      mbar_init(&own_empty[i], kTmaConsumerWarps);
+    }
+    for (int i = 0; i < NS; i++) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], kTmaConsumerWarps);
+    }
+    s_abort = 0;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(t.rec);
+    uint4* dst = reinterpret_cast<uint4*>(sRec);
+    const int n16 = (RS * 2 << g.b) / 16;
+    for (int i = tid; i < n16; i += kTmaThreads) dst[i] = __ldg(src + i);
+    const C* gFlo = reinterpret_cast<const C*>(t.F_lo);
+    const C* gCx = reinterpret_cast<const C*>(t.C_x);
+    for (int i = tid; i < (1 << g.b); i += kTmaThreads) sFlo[i] = gFlo[i];
+    for (int i = tid; i < (1 << g.n_cross); i += kTmaThreads) sCx[i] = gCx[i];
+  }
+  __syncthreads();
+  const int n_my = (g.n_groups - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+  const size_t esz = sizeof(S);
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane32 == 0) {
+      int q = 0;      // ring items issued
+      int n_own = 0;  // own tiles issued
+      bool ok = true;
+      for (int ord = 0; ord < n_my && ok; ord++) {
+        const GroupRec* G = t.grec + (int)blockIdx.x + ord * (int)gridDim.x;
+        const int r0 = G->r0, n_g = G->n_g;
+        if (ord >= 2 && !mbar_wait(&own_empty[ord & 1], (uint32_t)(((ord >> 1) - 1) & 1), &s_abort)) {
+          ok = false;
+          break;
+        }
+        {
+          const uint32_t bytes = (uint32_t)((size_t)n_g * W * esz);
+          mbar_expect_tx(&own_full[ord & 1], bytes + (uint32_t)sizeof(GroupRec));
+          bulk_load(&s_grp[ord & 1], G, (uint32_t)sizeof(GroupRec), &own_full[ord & 1]);
+          bulk_load(own + (size_t)(ord & 1) * stg, b1 + (size_t)r0 * W, bytes, &own_full[ord & 1]);
+          n_own++;
+        }
+        // items: cross blocks, high blocks, x, b2
+        const int n_items = MAXCR + G->n_hn + 2;
+        for (int it = 0; it < n_items && ok; it++) {
+          const S* src = nullptr;
+          int rows = 0;
+          if (it < MAXCR) {
+            if (it < g.n_cross && G->cr_n[it] > 0) {
+              src = b1 + (size_t)G->cr_base[it] * W;
+              rows = G->cr_n[it];
+            }
+          } else if (it < MAXCR + G->n_hn) {
+            src = b1 + (size_t)G->hn_base[it - MAXCR] * W;
+            rows = n_g;
+          } else if (it == MAXCR + G->n_hn) {
+            if (has_x) {
+              src = x + (size_t)r0 * W;
+              rows = n_g;
+            }
+          } else if (has_b2) {
+            src = b2 + (size_t)r0 * W;
+            rows = n_g;
+          }
+          if (!src) continue;
+          const int slot = q % NS;
+          if (q >= NS && !mbar_wait(&empty[slot], (uint32_t)(((q / NS) - 1) & 1), &s_abort)) {
+            ok = false;
+            break;
+          }
+          const uint32_t bytes = (uint32_t)((size_t)rows * W * esz);
+          mbar_expect_tx(&full[slot], bytes);
+          bulk_load(ring + (size_t)slot * stg, src, bytes, &full[slot]);
+          q++;
+        }
+      }
+      if (!ok) {
+        s_abort = 1;
+        atomicExch(err, 1);
+      }
+      // every copy already issued must land before the CTA may exit: wait for
+      // the last phase of each buffer that received one (bounded)
+      for (int sl = 0; sl < NS; sl++) {
+        const int uses = q > sl ? (q - 1 - sl) / NS + 1 : 0;
+        if (uses > 0)
+          for (uint32_t i = 0; i < (1u << 22); ++i)
+            if (mbar_try_wait(&full[sl], (uint32_t)((uses - 1) & 1))) break;
+      }
+      for (int b = 0; b < 2; b++) {
+        const int uses = n_own > b ? (n_own - 1 - b) / 2 + 1 : 0;
+        if (uses > 0)
+          for (uint32_t i = 0; i < (1u << 22); ++i)
+            if (mbar_try_wait(&own_full[b], (uint32_t)((uses - 1) & 1))) break;
+      }
+    }
+    return;
+  }
+
+  // -------------------------------------------------------------- consumers
+  const int ctid = tid - 32;
+  const int unit = ctid / LPR, lane = ctid % LPR;
+  // the two 16-byte chunks of a lane, ordered so that the two rows read by a
+  // quarter-warp fall on disjoint shared-memory banks
+  const int ch0 = (lane + 4 * (unit & 1)) * VEC, ch1 = (lane + 4 * (1 - (unit & 1))) * VEC;
+  const C* gFhi = reinterpret_cast<const C*>(t.F_hi);
+  int cr_lb[MAXCR], cr_c2[MAXCR];
+#pragma unroll
+  for (int k = 0; k < MAXCR; k++) {
+    cr_lb[k] = k < g.n_cross ? g.cross_lo[k] : 0;
+    cr_c2[k] = k < g.n_cross && g.cross_cls[k] == 2;
+  }
+  // accumulate the lane's two chunks of row `row` of buffer `p` into acc
+  auto acc2 = [&](A* acc, const S* p, size_t row) {
+    V16<S> u0, u1;
+    u0.i = *reinterpret_cast<const int4*>(p + row * W + ch0);
+    u1.i = *reinterpret_cast<const int4*>(p + row * W + ch1);
+#pragma unroll
+    for (int v = 0; v < VEC; v++) {
+      NT::acc(acc[v], u0.s[v]);
+      NT::acc(acc[VEC + v], u1.s[v]);
+    }
+  };
+  int q = 0;  // ring items consumed
+  C fhi_next = gFhi[blockIdx.x];  // diagonal constant of the group, schedule order (prefetched)
+  for (int ord = 0; ord < n_my; ord++) {
+    const int gidx = (int)blockIdx.x + ord * (int)gridDim.x;
+    const C fhi = fhi_next;
+    if (ord + 1 < n_my) fhi_next = gFhi[gidx + (int)gridDim.x];
+    if (!mbar_wait(&own_full[ord & 1], (uint32_t)((ord >> 1) & 1), &s_abort)) s_abort = 1;
+    if (s_abort) break;
+    const GroupRec* G = &s_grp[ord & 1];
+    const int r0 = G->r0, n_g = G->n_g, cls_base = G->cls_base;
+    const int n_hn = G->n_hn, n_hn1 = G->n_hn1, need = G->need_mask;
+    const S* tile = own + (size_t)(ord & 1) * stg;
+    A a1[RPT][VL], a2[RPT][VL];
+#pragma unroll
+    for (int i = 0; i < RPT; i++)
+#pragma unroll
+      for (int v = 0; v < VL; v++) {
+        a1[i][v] = NT::zero();
+        a2[i][v] = NT::zero();
+      }
+    uint32_t key[RPT];  // s_lo | cross pattern << 16
+    // ---- low bonds: gathers from the staged rows, neighbour lists from the record table
+#pragma unroll
+    for (int i = 0; i < RPT; i++) {
+      const int row = unit + UNITS * i;
+      const bool live = row < n_g;
+      const uint16_t* r = sRec + (size_t)(cls_base + (live ? row : 0)) * RS;
+      uint32_t rw[RS / 2];
+#pragma unroll
+      for (int qq = 0; qq < RS / 8; qq++) {
+        const uint4 v = reinterpret_cast<const uint4*>(r)[qq];
+        rw[4 * qq] = v.x;
+        rw[4 * qq + 1] = v.y;
+        rw[4 * qq + 2] = v.z;
+        rw[4 * qq + 3] = v.w;
+      }
+#define PF_E(e) ((rw[(e) >> 1] >> (((e)&1) * 16)) & 0xFFFFu)
+      const uint32_t s_lo = PF_E(0);
+      const uint32_t cnt = PF_E(1);
+      const int n1 = live ? (int)(cnt & 0xFF) : 0;
+      const int nl = live ? n1 + (J2 ? (int)(cnt >> 8) : 0) : 0;
+      uint32_t pattern = 0;
+#pragma unroll
+      for (int k = 0; k < MAXCR; k++)
+        if (live && k < g.n_cross && ((s_lo >> cr_lb[k]) & 1u) == ((need >> k) & 1)) pattern |= 1u << k;
+      key[i] = s_lo | (pattern << 16);
+      const int nmax = __reduce_max_sync(0xffffffffu, nl);
+#pragma unroll
+      for (int k0 = 0; k0 < LOWMAX; k0 += 2) {
+        if (k0 >= nmax) break;
+        V16<S> u[2][2];
+#pragma unroll
+        for (int j = 0; j < 2; j++) {
+          const int k = k0 + j;
+          if (k < LOWMAX && k < nl) {
+            const size_t rr = (size_t)PF_E(2 + k) * W;
+            u[j][0].i = *reinterpret_cast<const int4*>(tile + rr + ch0);
+            u[j][1].i = *reinterpret_cast<const int4*>(tile + rr + ch1);
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < 2; j++) {
+          const int k = k0 + j;
+          if (k < LOWMAX && k < nl) {
+            A* acc = (!J2 || k < n1) ? a1[i] : a2[i];
+#pragma unroll
+            for (int v = 0; v < VEC; v++) {
+              NT::acc(acc[v], u[j][0].s[v]);
+              NT::acc(acc[VEC + v], u[j][1].s[v]);
+            }
+          }
+        }
+      }
+#undef PF_E
+    }
+    // ---- ring items in the producer's order: cross blocks, high blocks, x, b2
+    int x_slot = -1, b2_slot = -1;
+    for (int k = 0; k < MAXCR; k++) {
+      if (!(k < g.n_cross && G->cr_n[k] > 0)) continue;
+      const int slot = q % NS;
+      if (!mbar_wait(&full[slot], (uint32_t)((q / NS) & 1), &s_abort)) s_abort = 1;
+      if (s_abort) break;
+      const S* blk = ring + (size_t)slot * stg;
+      const bool c1 = !J2 || !cr_c2[k];
+#pragma unroll
+      for (int i = 0; i < RPT; i++) {
+        if ((key[i] >> (16 + k)) & 1u) {
+          const int row = unit + UNITS * i;
+          const uint16_t* r = sRec + (size_t)(cls_base + row) * RS;
+          acc2(c1 ? a1[i] : a2[i], blk, r[RS - 1 - k]);
+        }
+      }
+      __syncwarp();
+      if (lane32 == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[slot])) : "memory");
+      q++;
+    }
+    if (s_abort) break;
+    for (int k = 0; k < n_hn; k++) {
+      const int slot = q % NS;
+      if (!mbar_wait(&full[slot], (uint32_t)((q / NS) & 1), &s_abort)) s_abort = 1;
+      if (s_abort) break;
+      const S* blk = ring + (size_t)slot * stg;
+      const bool c1 = !J2 || k < n_hn1;
+#pragma unroll
+      for (int i = 0; i < RPT; i++) {
+        const int row = unit + UNITS * i;
+        if (row < n_g) acc2(c1 ? a1[i] : a2[i], blk, row);
+      }
+      __syncwarp();
+      if (lane32 == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[slot])) : "memory");
+      q++;
+    }
+    if (s_abort) break;
+    if (has_x) {
+      x_slot = q % NS;
+      if (!mbar_wait(&full[x_slot], (uint32_t)((q / NS) & 1), &s_abort)) s_abort = 1;
+      q++;
+    }
+    if (has_b2 && !s_abort) {
+      b2_slot = q % NS;
+      if (!mbar_wait(&full[b2_slot], (uint32_t)((q / NS) & 1), &s_abort)) s_abort = 1;
+      q++;
+    }
+    if (s_abort) break;
+    // ---- diagonal, combination, store
+#pragma unroll
+    for (int i = 0; i < RPT; i++) {
+      const int row = unit + UNITS * i;
+      if (row < n_g) {
+        const uint32_t s_lo = key[i] & 0xFFFFu, pattern = key[i] >> 16;
+        const C ad = NT::add3(sFlo[s_lo], fhi, sCx[pattern]);
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+          const size_t lo = (size_t)row * W + (h ? ch1 : ch0);
+          V16<S> xo, xv, bv, res;
+          xo.i = *reinterpret_cast<const int4*>(tile + lo);
+          if (has_x) xv.i = *reinterpret_cast<const int4*>(ring + (size_t)x_slot * stg + lo);
+          if (has_b2) bv.i = *reinterpret_cast<const int4*>(ring + (size_t)b2_slot * stg + lo);
+#pragma unroll
+          for (int v = 0; v < VEC; v++)
+            res.s[v] = NT::combine(has_x ? xv.s[v] : S(), xo.s[v], has_b2 ? bv.s[v] : S(), a1[i][h * VEC + v],
+                                   a2[i][h * VEC + v], ad, kc, has_x, has_b2, J2);
+          __stcg(reinterpret_cast<int4*>(out + (size_t)(r0 + row) * W + (h ? ch1 : ch0)), res.i);
+        }
+      }
+    }
+    __syncwarp();
+    if (lane32 == 0) {
+      if (x_slot >= 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[x_slot])) : "memory");
+      if (b2_slot >= 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[b2_slot])) : "memory");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&own_empty[ord & 1])) : "memory");
+    }
+  }
+  if (s_abort && ctid == 0) atomicExch(err, 1);
 }
 
 // ------------------------------------------------------ slice conversions
@@ -705,7 +1122,8 @@ int HamPlan::init(const polfed_model* m, cudaStream_t s, bool stream_ordered, in
   };
   const size_t oTlo = carve(nlo * 2), oUlo = carve(nlo * 2), oThi = carve(nhi * 4), oOrd = carve(nhi * 4),
                oFlo = carve(nlo * 8), oFhi = carve(nhi * 8), oCx = carve(ncx * 8),
-               oRec = carve(nlo * (size_t)geo.rec_stride * 2);
+               oRec = carve(nlo * (size_t)geo.rec_stride * 2), oGrp = carve((size_t)geo.n_groups * sizeof(GroupRec)),
+               oErr = carve(64);
   stream_alloc = stream_ordered;
   if (stream_ordered)
     PF_CUDA(cudaMallocAsync(&dev, bytes, s));
@@ -720,6 +1138,9 @@ int HamPlan::init(const polfed_model* m, cudaStream_t s, bool stream_ordered, in
   tab.F_hi = (double*)(d + oFhi);
   tab.C_x = (double*)(d + oCx);
   tab.rec = (uint16_t*)(d + oRec);
+  tab.grec = (GroupRec*)(d + oGrp);
+  err_flag = (int*)(d + oErr);
+  PF_CUDA(cudaMemsetAsync(err_flag, 0, 64, s));
   k_tables_lo<<<(unsigned)((nlo + 255) / 256), 256, 0, s>>>(geo, tab.T_lo, tab.U_lo, tab.F_lo);
   k_tables_rec<<<(unsigned)((nlo + 255) / 256), 256, 0, s>>>(geo, tab.T_lo, tab.rec);
   k_tables_hi<<<(unsigned)((nhi + 255) / 256), 256, 0, s>>>(geo, tab.T_hi, tab.F_hi);
@@ -739,6 +1160,8 @@ int HamPlan::init(const polfed_model* m, cudaStream_t s, bool stream_ordered, in
     for (uint32_t grp = 0; grp < (uint32_t)nhi; grp++)
       if (__builtin_popcount(grp) == c.second) order.push_back((int32_t)grp);
   PF_CUDA(cudaMemcpyAsync(tab.order, order.data(), order.size() * 4, cudaMemcpyHostToDevice, s));
+  k_tables_groups<<<(unsigned)((geo.n_groups + 127) / 128), 128, 0, s>>>(geo, tab.T_hi, tab.order, tab.grec);
+  PF_CUDA(cudaGetLastError());
   PF_CUDA(cudaStreamSynchronize(s));  // host vector goes out of scope
   return POLFED_OK;
 }
@@ -754,7 +1177,8 @@ int HamPlan::prepare_typed(int kind, double e_lo, double e_hi) {
   }
   const size_t nlo = (size_t)1 << geo.b, nhi = (size_t)1 << geo.nh, ncx = (size_t)1 << geo.n_cross;
   const size_t es = typed_size(kind);
-  const size_t need = (nlo + nhi + ncx) * es + 512;
+  const size_t ngr = (size_t)geo.n_groups;
+  const size_t need = (nlo + nhi + ncx + ngr) * es + 512;
   if (!typed[kind] || typed_bytes[kind] < need) {
     if (typed[kind]) {
       if (stream_alloc)
@@ -771,11 +1195,13 @@ int HamPlan::prepare_typed(int kind, double e_lo, double e_hi) {
   }
   // scale on the host: copy the FP64 tables back (small), convert, upload
   std::vector<double> flo(nlo), fhi(nhi), cx(ncx);
+  std::vector<int32_t> ord(ngr);
   PF_CUDA(cudaMemcpyAsync(flo.data(), tab.F_lo, nlo * 8, cudaMemcpyDeviceToHost, stream));
   PF_CUDA(cudaMemcpyAsync(fhi.data(), tab.F_hi, nhi * 8, cudaMemcpyDeviceToHost, stream));
   PF_CUDA(cudaMemcpyAsync(cx.data(), tab.C_x, ncx * 8, cudaMemcpyDeviceToHost, stream));
+  PF_CUDA(cudaMemcpyAsync(ord.data(), tab.order, ngr * 4, cudaMemcpyDeviceToHost, stream));
   PF_CUDA(cudaStreamSynchronize(stream));
-  std::vector<unsigned char> buf((nlo + nhi + ncx) * es);
+  std::vector<unsigned char> buf((nlo + nhi + ncx + ngr) * es);
   size_t pos = 0;
   auto put = [&](double v) {
     if (kind == POLFED_F32) {
@@ -794,6 +1220,7 @@ int HamPlan::prepare_typed(int kind, double e_lo, double e_hi) {
   for (size_t i = 0; i < nlo; i++) put(alpha * flo[i]);
   for (size_t i = 0; i < nhi; i++) put(alpha * (fhi[i] - beta));
   for (size_t i = 0; i < ncx; i++) put(alpha * cx[i]);
+  for (size_t i = 0; i < ngr; i++) put(alpha * (fhi[ord[i]] - beta));  // F_hi in schedule order
   PF_CUDA(cudaMemcpyAsync(typed[kind], buf.data(), buf.size(), cudaMemcpyHostToDevice, stream));
   PF_CUDA(cudaStreamSynchronize(stream));
   typed_ok[kind] = true;
@@ -826,6 +1253,14 @@ void HamPlan::release() {
 static void split_df(double v, float2& o) {
   o.x = (float)v;
   o.y = (float)(v - (double)o.x);
+}
+
+// 0 or +-2^k (with k in the float exponent range): scaling by it is exact
+static bool pow2_or_zero(double v) {
+  if (v == 0.0) return true;
+  int e = 0;
+  const double m = std::frexp(std::fabs(v), &e);
+  return m == 0.5 && e > -120 && e < 120;
 }
 
 template <class NT, int LPR, bool J2>
@@ -870,7 +1305,7 @@ static int launch_step_t(const HamPlan& p, const StepArgs& a, cudaStream_t s) {
   }
   if (occ < 1) return fail(POLFED_EINVAL, "step kernel cannot be resident (shared memory)");
   int grid = std::min(g.n_groups, nsm * occ);
-  StepTables t{p.tab.rec, p.tab.T_hi, p.tab.order, nullptr, nullptr, nullptr};
+  StepTables t{p.tab.rec, p.tab.grec, nullptr, nullptr, nullptr, p.tab.order};
   if (g.rec_stride != (J2 ? 32 : 16)) return fail(POLFED_EINVAL, "record layout does not match the kernel");
   const size_t es = sizeof(C);
   const char* base = (const char*)p.typed[std::is_same<NT, NF32>::value ? POLFED_F32 : (std::is_same<NT, NF64>::value ? POLFED_F64 : POLFED_DF64)];
@@ -887,6 +1322,7 @@ static int launch_step_t(const HamPlan& p, const StepArgs& a, cudaStream_t s) {
     split_df(a.cB, kc.cB);
     split_df(o1, kc.o1);
     split_df(o2, kc.o2);
+    kc.exact = pow2_or_zero(a.cX) && pow2_or_zero(a.cH) && pow2_or_zero(a.cB);
   } else {
     kc.cX = (C)a.cX;
     kc.cH = (C)a.cH;
@@ -904,9 +1340,85 @@ static int launch_step_t(const HamPlan& p, const StepArgs& a, cudaStream_t s) {
   return POLFED_OK;
 }
 
+static size_t tma_smem_bytes(const HamGeometry& g, size_t esz_c, bool j2) {
+  const size_t stg = (size_t)g.max_group * 128;
+  return (2 + tma_stages(j2)) * stg + ((size_t)g.rec_stride * 2 << g.b) +
+         (((size_t)1 << g.b) + ((size_t)1 << g.n_cross)) * esz_c;
+}
+
+static bool tma_disabled() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = getenv("POLFED_NO_TMA");
+    v = (e && e[0] == '1') ? 1 : 0;
+  }
+  return v == 1;
+}
+
+template <class NT, bool J2>
+static int launch_step_tma(const HamPlan& p, const StepArgs& a, cudaStream_t s) {
+  using S = typename NT::S;
+  using C = typename NT::C;
+  const HamGeometry& g = p.geo;
+  const size_t smem = tma_smem_bytes(g, sizeof(C), J2);
+  auto kern = k_ham_step_tma<NT, J2>;
+  static int configured[64] = {0};
+  static int nsm_cache[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 64 && !configured[dev]) {
+    int optin = 0;
+    PF_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    cudaFuncAttributes fa;
+    PF_CUDA(cudaFuncGetAttributes(&fa, kern));
+    PF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes));
+    cudaDeviceGetAttribute(&nsm_cache[dev], cudaDevAttrMultiProcessorCount, dev);
+    configured[dev] = 1;
+  }
+  const int nsm = dev < 64 ? nsm_cache[dev] : 152;
+  const int grid = std::min(g.n_groups, nsm);
+  const int kk = std::is_same<NT, NF32>::value ? POLFED_F32 : (std::is_same<NT, NF64>::value ? POLFED_F64 : POLFED_DF64);
+  StepTables t{p.tab.rec, p.tab.grec, nullptr, nullptr, nullptr, p.tab.order};
+  const size_t es = sizeof(C);
+  const char* base = (const char*)p.typed[kk];
+  t.F_lo = base;
+  t.F_hi = base + ((size_t)1 << g.b) * es;
+  t.C_x = base + (((size_t)1 << g.b) + ((size_t)1 << g.nh)) * es;
+  t.F_hi = base + (((size_t)1 << g.b) + ((size_t)1 << g.nh) + ((size_t)1 << g.n_cross)) * es;  // schedule order
+  typename NT::KC kc;
+  const double alpha = (p.typed_lo[kk] == 0.0 && p.typed_hi[kk] == 0.0) ? 1.0 : 2.0 / (p.typed_hi[kk] - p.typed_lo[kk]);
+  const double o1 = alpha * 0.5 * g.J1, o2 = alpha * 0.5 * g.J2;
+  if constexpr (std::is_same<NT, NDF>::value) {
+    split_df(a.cX, kc.cX);
+    split_df(a.cH, kc.cH);
+    split_df(a.cB, kc.cB);
+    split_df(o1, kc.o1);
+    split_df(o2, kc.o2);
+    kc.exact = pow2_or_zero(a.cX) && pow2_or_zero(a.cH) && pow2_or_zero(a.cB);
+  } else {
+    kc.cX = (C)a.cX;
+    kc.cH = (C)a.cH;
+    kc.cB = (C)a.cB;
+    kc.o1 = (C)o1;
+    kc.o2 = (C)o2;
+  }
+  kern<<<grid, kTmaThreads, smem, s>>>(g, t, (const S*)a.b1, (const S*)a.b2, (const S*)a.x, (S*)a.out, kc,
+                                       a.cX != 0.0 && a.x != nullptr, a.cB != 0.0 && a.b2 != nullptr, p.err_flag);
+  PF_CUDA(cudaGetLastError());
+  Counters& cn = counters();
+  cn.launches++;
+  cn.step_launches++;
+  cn.step_alg_bytes += (double)g.dim * 128.0 * (3.0 + (a.cX != 0.0 ? 1.0 : 0.0));
+  return POLFED_OK;
+}
+
 template <class NT>
 static int launch_step_n(const HamPlan& p, const StepArgs& a, cudaStream_t s) {
   const bool j2 = p.geo.n_low2 + p.geo.n_high2 > 0 || p.geo.J2 != 0.0;
+  if (a.lpr == 8 && !tma_disabled() && p.geo.max_group <= kTmaRowsPerThread * (32 * kTmaConsumerWarps / 4) &&
+      tma_smem_bytes(p.geo, sizeof(typename NT::C), j2) <= 220 * 1024 && p.geo.max_group >= 32 &&
+      p.geo.rec_stride == (j2 ? 32 : 16))
+    return j2 ? launch_step_tma<NT, true>(p, a, s) : launch_step_tma<NT, false>(p, a, s);
   switch (a.lpr) {
 #define PF_CASE(L_)                                                               \
   case L_:                                                                        \
@@ -1035,6 +1547,18 @@ struct StepTimer {
   }
 };
 
+// A step kernel whose bounded wait expired leaves plan.err_flag set.
+static int check_timeout(HamPlan& plan, cudaStream_t s) {
+  int e = 0;
+  PF_CUDA(cudaMemcpyAsync(&e, plan.err_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  PF_CUDA(cudaStreamSynchronize(s));
+  if (e) {
+    cudaMemsetAsync(plan.err_flag, 0, sizeof(int), s);
+    return fail(POLFED_ETIMEOUT, "a bounded device wait in the step kernel expired");
+  }
+  return POLFED_OK;
+}
+
 int filter_block(HamPlan& plan, int kind, const double* c, int K, double invD, const void* in, void* out, int n_b,
                  int abi_kind, FilterScratch& scr, cudaStream_t s, int lpr_hint) {
   const int lpr = lpr_hint > 0 ? lpr_hint : choose_lpr(kind, n_b);
@@ -1065,6 +1589,7 @@ int filter_block(HamPlan& plan, int kind, const double* c, int K, double invD, c
     StepArgs a{cur, oth, scr.xs, oth, c[0] * invD, invD, (K == 1) ? 0.0 : -invD, lpr};
     PF_CHECK(launch_ham_step(plan, kind, a, s));
     PF_CHECK(tm.stop());
+    PF_CHECK(check_timeout(plan, s));
     PF_CHECK(slice_out(kind, abi_kind, oth, dim, W, ncols, out, n_b, col0, scr.flag, s));
   }
   return POLFED_OK;
@@ -1085,6 +1610,7 @@ int apply_block(HamPlan& plan, int kind, const void* in, void* out, int n_b, int
     PF_CHECK(launch_ham_step(plan, kind, a, s));
     PF_CHECK(slice_out(kind, abi_kind, scr.ba, dim, W, ncols, out, n_b, col0, scr.flag, s));
   }
+  PF_CHECK(check_timeout(plan, s));
   return POLFED_OK;
 }
 

@@ -89,10 +89,22 @@ struct HamTables {
   double* F_hi;     // [2^nh] diagonal part from high bonds and high fields
   double* C_x;      // [2^n_cross] diagonal part from cross bonds by "differ" pattern
   // [2^b * rec_stride] per-row neighbour record, indexed by cls_off[c] + local index:
-  //   entry 0: s_lo; entries 1..: local index of each low-bond neighbour (0xFFFF if the
-  //   pair is parallel); last entries (from the end): local index, in the neighbouring
-  //   popcount class, of s_lo with the low site of cross bond k flipped
+  //   entry 0: s_lo; entry 1: n1 | n2 << 8 (active low bonds of class 1 and 2);
+  //   entries 2..: local indices of the active low-bond neighbours, class 1 first;
+  //   last entries (from the end): local index, in the neighbouring popcount
+  //   class, of s_lo with the low site of cross bond k flipped
   uint16_t* rec;
+  // [n_groups] per-group constants in schedule order (see GroupRec)
+  struct GroupRec* grec;
+};
+
+constexpr int kMaxHigh = 24;
+// Per-group constants (one group = rows sharing s_hi), precomputed per plan.
+struct alignas(16) GroupRec {
+  int r0, n_g, cls_base, n_hn1, n_hn, need_mask, pad0, pad1;
+  int hn_base[kMaxHigh];  // first row of each neighbouring group through an antiparallel high bond
+  int cr_base[8];         // first row of the group reached through cross bond k
+  int cr_n[8];            // rows of that group (0 if no row of this group has the bond antiparallel)
 };
 
 int build_geometry(const polfed_model* m, int b_override, HamGeometry* g);
@@ -102,6 +114,7 @@ class HamPlan {
   HamGeometry geo;
   HamTables tab{};
   void* dev = nullptr;       // one allocation for all tables
+  int* err_flag = nullptr;   // set by a kernel whose bounded wait expired
   // per-precision alpha/beta-scaled tables (F_lo, F_hi, C_x), indexed by dtype
   void* typed[3] = {nullptr, nullptr, nullptr};
   size_t typed_bytes[3] = {0, 0, 0};
