@@ -147,6 +147,33 @@ int polfed_cheb_filter(const polfed_model* model, const uint32_t* d_states, int6
                        double sigma, int32_t K, const double* coeffs, const void* d_X, void* d_Y, int32_t n_b,
                        int32_t dtype, polfed_stream_t stream);
 
+/* Allocation-free variant of polfed_cheb_filter (the paper has no
+ * counterpart; this is a service for callers).  Some callers cannot allocate
+ * device memory while they run: code executing inside an allocator or memory
+ * pool callback, a host application that owns every device allocation
+ * itself, or a latency-critical loop that must never enter the allocator.
+ * This call takes the same arguments and computes the same Y as
+ * polfed_cheb_filter, but it allocates and frees no device memory (and no
+ * host memory on its normal path): its operator tables and Clenshaw buffers
+ * are carved out of one fixed 32 MiB device array that every GPU using this
+ * library holds from the moment the library's device code is loaded until
+ * the process exits.
+ *   Limit: the tables plus three dim x 128-byte slice buffers must fit in
+ *          32 MiB, i.e. L <= 18 (dim <= 48620) for any n_b; larger problems
+ *          return POLFED_ENOMEM with a message naming the bytes needed.
+ *   First call on a device: looks up the array's device address
+ *          (cudaGetSymbolAddress) with that device current; make this first
+ *          call before any stream capture.
+ *   Sharing: every call uses the same array and leaves its last contents in
+ *          it; each call rewrites everything it reads (tables, recurrence
+ *          buffers, flags), so nothing carries over.  Calls that overlap on
+ *          the GPU (other streams, other host threads) race on the array and
+ *          must be serialized by the caller.
+ * Synchronizes the stream before returning. */
+int polfed_cheb_filter_static(const polfed_model* model, const uint32_t* d_states, int64_t dim, double e_lo,
+                              double e_hi, double sigma, int32_t K, const double* coeffs, const void* d_X, void* d_Y,
+                              int32_t n_b, int32_t dtype, polfed_stream_t stream);
+
 /* Context: device, stream, cuSOLVER handle and reusable device workspace.
  *   device          : CUDA device ordinal (the context makes it current in its calls).
  *   workspace_bytes : advisory upper bound for the context's device workspace

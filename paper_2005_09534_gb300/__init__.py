@@ -28,6 +28,7 @@ POLFED_ETIMEOUT = -6
 F64, F32, DF64 = 0, 1, 2
 
 EXPORTED = ["polfed_opts_default", "polfed_basis_build", "polfed_h_apply", "polfed_cheb_filter",
+            "polfed_cheb_filter_static",
             "polfed_ctx_create", "polfed_ctx_destroy", "polfed_ctx_set_stream", "polfed_block_lanczos",
             "polfed_eigs", "polfed_last_error"]
 
@@ -82,6 +83,7 @@ def load(path: str = LIB_PATH):
                                    c_int32, c_int32, c_void_p]
     lib.polfed_cheb_filter.argtypes = [POINTER(CModel), c_void_p, c_int64, c_double, c_double, c_double, c_int32,
                                        POINTER(c_double), c_void_p, c_void_p, c_int32, c_int32, c_void_p]
+    lib.polfed_cheb_filter_static.argtypes = lib.polfed_cheb_filter.argtypes
     lib.polfed_ctx_create.argtypes = [c_int32, c_size_t, POINTER(c_void_p)]
     lib.polfed_ctx_destroy.argtypes = [c_void_p]
     lib.polfed_ctx_destroy.restype = None
@@ -167,6 +169,21 @@ def cheb_filter(model, d_states, dim, e_lo, e_hi, sigma, K, X, Y, n_b, dtype, co
     rc = load().polfed_cheb_filter(byref(m.c), _ptr(d_states), int(dim), float(e_lo), float(e_hi), float(sigma),
                                    int(K), cptr, _ptr(X), _ptr(Y), int(n_b), int(dtype), _stream(stream))
     return _check(rc, allow=(POLFED_EBOUNDS,) if allow_bounds_error else ())
+
+
+def cheb_filter_static(model, d_states, dim, e_lo, e_hi, sigma, K, X, Y, n_b, dtype, coeffs=None, stream=None):
+    """polfed_cheb_filter_static: the filter without any device allocation (fixed
+    32 MiB device array shared by all calls; L <= 18)."""
+    m = Model.of(model)
+    cptr = None
+    if coeffs is not None:
+        coeffs = np.ascontiguousarray(np.asarray(coeffs, dtype=np.float64))
+        assert coeffs.shape == (int(K) + 1,)
+        cptr = coeffs.ctypes.data_as(POINTER(c_double))
+    rc = load().polfed_cheb_filter_static(byref(m.c), _ptr(d_states), int(dim), float(e_lo), float(e_hi),
+                                          float(sigma), int(K), cptr, _ptr(X), _ptr(Y), int(n_b), int(dtype),
+                                          _stream(stream))
+    return _check(rc)
 
 
 class Ctx:

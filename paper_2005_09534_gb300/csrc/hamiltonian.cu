@@ -1661,3 +1661,267 @@ int launch_basis(int L, int n_up, uint32_t* d_states, int64_t dim, cudaStream_t 
 }
 
 }  // namespace polfed
+
+// ===================================================================== no-alloc
+// polfed_cheb_filter_static: the Chebyshev filter with every table and every
+// recurrence buffer carved out of one fixed device array instead of allocated
+// memory.  It exists for callers that cannot allocate device memory while they
+// run, e.g. code executing inside a memory pool or allocator callback, a
+// library embedded in a host application that owns all device allocations, or
+// a real-time loop that must not call into the allocator.  The array is a
+// file-scope __device__ object: every GPU that loads this library holds it
+// (kStaticScratchBytes) until the process exits, whether or not it is used.
+namespace polfed {
+
+constexpr size_t kStaticScratchBytes = (size_t)32 << 20;  // 32 MiB: dim <= 48620 (L <= 18) at 128-byte slices
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+// Device address of g_static_scratch per device (host code must not use the
+// symbol itself: on the host it names a stand-in, not device memory).
+static void* g_static_addr[64] = {nullptr};
+static std::mutex g_static_mu;
+
+static int static_scratch_addr(void** out) {
+  int dev = 0;
+  PF_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(POLFED_EINVAL, "device ordinal out of range for the static scratch table");
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (!g_static_addr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess) return fail(POLFED_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    g_static_addr[dev] = p;
+  }
+  *out = g_static_addr[dev];
+  return POLFED_OK;
+}
+
+// Schedule order of the groups on the device: classes (popcount of s_hi) by
+// decreasing group size, groups of a class in ascending s_hi (same order as
+// HamPlan::init builds on the host).
+__global__ void k_static_order(const HamGeometry g, const int32_t* cls_start, int32_t* order) {
+  const int grp = blockIdx.x * blockDim.x + threadIdx.x;
+  if (grp >= (1 << g.nh)) return;
+  const int pc = __popc(grp);
+  const int n_lo = g.n_up - pc;
+  if (n_lo < 0 || n_lo > g.b) return;
+  uint32_t r = 0;
+  int k = 0;
+  for (int q = 0; q < g.nh; q++)
+    if ((grp >> q) & 1) r += c_binom[q][++k];  // rank among nh-bit strings of popcount pc
+  order[cls_start[pc] + (int)r] = grp;
+}
+
+// Typed, alpha/beta-scaled diagonal tables (same layout prepare_typed writes).
+template <class NT>
+__global__ void k_static_typed(const double* F_lo, const double* F_hi, const double* C_x, const int32_t* order,
+                               int nlo, int nhi, int ncx, int ngr, double alpha, double beta, typename NT::C* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = nlo + nhi + ncx + ngr;
+  if (i >= n) return;
+  double v;
+  if (i < nlo)
+    v = alpha * F_lo[i];
+  else if (i < nlo + nhi)
+    v = alpha * (F_hi[i - nlo] - beta);
+  else if (i < nlo + nhi + ncx)
+    v = alpha * C_x[i - nlo - nhi];
+  else
+    v = alpha * (F_hi[order[i - nlo - nhi - ncx]] - beta);
+  out[i] = Conv<NT>::from_d(v);
+}
+
+// c_n of Eq. (2) computed on the fly (same expression as cheb_coeffs) or read
+// from the caller's array; no storage.
+struct CoefSource {
+  const double* user;
+  double sigma, phi;
+  double operator[](int n) const {
+    if (user) return user[n];
+    const double cn = (sigma == 0.0) ? ((n & 1) ? 0.0 : ((n / 2) & 1 ? -1.0 : 1.0)) : std::cos(n * phi);
+    return (n == 0 ? 1.0 : 2.0) * cn;
+  }
+  double T(int n) const {  // T_n(sigma)
+    return (sigma == 0.0) ? ((n & 1) ? 0.0 : ((n / 2) & 1 ? -1.0 : 1.0)) : std::cos(n * phi);
+  }
+};
+
+static int static_filter(const polfed_model* model, double e_lo, double e_hi, const CoefSource& c, int K, double invD,
+                         const void* d_X, void* d_Y, int n_b, int dtype, cudaStream_t s) {
+  upload_binomials();
+  HamPlan plan;  // borrowed memory: pointers are cleared before it is destroyed
+  struct Unborrow {
+    HamPlan& p;
+    ~Unborrow() {
+      p.dev = nullptr;
+      for (int k = 0; k < 3; k++) p.typed[k] = nullptr;
+    }
+  } unborrow{plan};
+  PF_CHECK(build_geometry(model, -1, &plan.geo));
+  const HamGeometry& g = plan.geo;
+  const size_t nlo = (size_t)1 << g.b, nhi = (size_t)1 << g.nh, ncx = (size_t)1 << g.n_cross;
+  const int lpr = choose_lpr(dtype, n_b);
+  const size_t es_c = dtype == POLFED_F32 ? 4 : 8;
+  size_t bytes = 0;
+  auto carve = [&](size_t n) {
+    size_t o = bytes;
+    bytes += (n + 255) & ~(size_t)255;
+    return o;
+  };
+  const size_t oTlo = carve(nlo * 2), oUlo = carve(nlo * 2), oThi = carve(nhi * 4), oOrd = carve(nhi * 4),
+               oFlo = carve(nlo * 8), oFhi = carve(nhi * 8), oCx = carve(ncx * 8),
+               oRec = carve(nlo * (size_t)g.rec_stride * 2), oGrp = carve((size_t)g.n_groups * sizeof(GroupRec)),
+               oErr = carve(64), oCls = carve(34 * 4), oTyp = carve((nlo + nhi + ncx + (size_t)g.n_groups) * es_c),
+               oScr = carve(filter_scratch_bytes(plan, dtype, lpr));
+  if (bytes > kStaticScratchBytes)
+    return fail(POLFED_ENOMEM, "polfed_cheb_filter_static needs " + std::to_string(bytes) +
+                                   " bytes of scratch; the static array holds " + std::to_string(kStaticScratchBytes) +
+                                   " (use polfed_cheb_filter for this size)");
+  void* base = nullptr;
+  PF_CHECK(static_scratch_addr(&base));
+  char* d = (char*)base;
+  plan.stream = s;
+  plan.stream_alloc = false;
+  plan.tab.T_lo = (uint16_t*)(d + oTlo);
+  plan.tab.U_lo = (uint16_t*)(d + oUlo);
+  plan.tab.T_hi = (int32_t*)(d + oThi);
+  plan.tab.order = (int32_t*)(d + oOrd);
+  plan.tab.F_lo = (double*)(d + oFlo);
+  plan.tab.F_hi = (double*)(d + oFhi);
+  plan.tab.C_x = (double*)(d + oCx);
+  plan.tab.rec = (uint16_t*)(d + oRec);
+  plan.tab.grec = (GroupRec*)(d + oGrp);
+  plan.err_flag = (int*)(d + oErr);
+  // group schedule: class start offsets (host arithmetic on fixed arrays only)
+  int32_t cls_start[34] = {0};
+  {
+    int pcs[34], sizes[34], n = 0;
+    for (int pc = 0; pc <= g.nh; pc++) {
+      const int n_lo = g.n_up - pc;
+      if (n_lo < 0 || n_lo > g.b) continue;
+      pcs[n] = pc;
+      sizes[n] = (int)binom_host(g.b, n_lo);
+      n++;
+    }
+    for (int i = 1; i < n; i++)  // stable insertion sort by decreasing size
+      for (int j = i; j > 0 && sizes[j] > sizes[j - 1]; j--) {
+        std::swap(sizes[j], sizes[j - 1]);
+        std::swap(pcs[j], pcs[j - 1]);
+      }
+    int pos = 0;
+    for (int i = 0; i < n; i++) {
+      cls_start[pcs[i]] = pos;
+      pos += (int)binom_host(g.nh, pcs[i]);
+    }
+  }
+  int32_t* d_cls = (int32_t*)(d + oCls);
+  PF_CUDA(cudaMemcpyAsync(d_cls, cls_start, sizeof(cls_start), cudaMemcpyHostToDevice, s));
+  PF_CUDA(cudaMemsetAsync(plan.err_flag, 0, 64, s));
+  k_tables_lo<<<(unsigned)((nlo + 255) / 256), 256, 0, s>>>(g, plan.tab.T_lo, plan.tab.U_lo, plan.tab.F_lo);
+  k_tables_rec<<<(unsigned)((nlo + 255) / 256), 256, 0, s>>>(g, plan.tab.T_lo, plan.tab.rec);
+  k_tables_hi<<<(unsigned)((nhi + 255) / 256), 256, 0, s>>>(g, plan.tab.T_hi, plan.tab.F_hi);
+  k_tables_cx<<<(unsigned)((ncx + 255) / 256), 256, 0, s>>>(g, plan.tab.C_x);
+  k_static_order<<<(unsigned)((nhi + 255) / 256), 256, 0, s>>>(g, d_cls, plan.tab.order);
+  k_tables_groups<<<(unsigned)((g.n_groups + 127) / 128), 128, 0, s>>>(g, plan.tab.T_hi, plan.tab.order, plan.tab.grec);
+  PF_CUDA(cudaGetLastError());
+  double alpha = 1.0, beta = 0.0;
+  if (!(e_lo == 0.0 && e_hi == 0.0)) {
+    alpha = 2.0 / (e_hi - e_lo);
+    beta = 0.5 * (e_hi + e_lo);
+  }
+  const int ntyp = (int)(nlo + nhi + ncx) + g.n_groups;
+  void* typ = d + oTyp;
+  if (dtype == POLFED_F32)
+    k_static_typed<NF32><<<(ntyp + 255) / 256, 256, 0, s>>>(plan.tab.F_lo, plan.tab.F_hi, plan.tab.C_x, plan.tab.order,
+                                                             (int)nlo, (int)nhi, (int)ncx, g.n_groups, alpha, beta,
+                                                             (float*)typ);
+  else if (dtype == POLFED_F64)
+    k_static_typed<NF64><<<(ntyp + 255) / 256, 256, 0, s>>>(plan.tab.F_lo, plan.tab.F_hi, plan.tab.C_x, plan.tab.order,
+                                                             (int)nlo, (int)nhi, (int)ncx, g.n_groups, alpha, beta,
+                                                             (double*)typ);
+  else
+    k_static_typed<NDF><<<(ntyp + 255) / 256, 256, 0, s>>>(plan.tab.F_lo, plan.tab.F_hi, plan.tab.C_x, plan.tab.order,
+                                                           (int)nlo, (int)nhi, (int)ncx, g.n_groups, alpha, beta,
+                                                           (float2*)typ);
+  PF_CUDA(cudaGetLastError());
+  plan.typed[dtype] = typ;
+  plan.typed_ok[dtype] = true;
+  plan.typed_lo[dtype] = e_lo;
+  plan.typed_hi[dtype] = e_hi;
+  // Clenshaw recurrence, slice by slice (same steps as filter_block)
+  FilterScratch scr;
+  scr.xs = d + oScr;
+  scr.bytes = filter_scratch_bytes(plan, dtype, lpr);
+  carve_scratch(scr, plan, dtype, lpr);
+  const int W = slice_width(dtype, lpr);
+  const int abi = dtype == POLFED_F32 ? POLFED_F32 : POLFED_F64;
+  PF_CUDA(cudaMemsetAsync(scr.flag, 0, 16, s));
+  for (int col0 = 0; col0 < n_b; col0 += W) {
+    const int ncols = std::min(W, n_b - col0);
+    if (K == 0) {
+      PF_CHECK(slice_in(dtype, abi, d_X, g.dim, n_b, col0, ncols, W, nullptr, scr.ba, nullptr, c[0] * invD, scr.flag, s));
+      PF_CHECK(slice_out(dtype, abi, scr.ba, g.dim, W, ncols, d_Y, n_b, col0, scr.flag, s));
+      continue;
+    }
+    PF_CHECK(slice_in(dtype, abi, d_X, g.dim, n_b, col0, ncols, W, scr.xs, scr.ba, scr.bb, c[K], scr.flag, s));
+    void* cur = scr.ba;
+    void* oth = scr.bb;
+    for (int k = K - 1; k >= 1; k--) {
+      StepArgs a{cur, oth, scr.xs, oth, c[k], 2.0, (k == K - 1) ? 0.0 : -1.0, lpr};
+      PF_CHECK(launch_ham_step(plan, dtype, a, s));
+      std::swap(cur, oth);
+    }
+    StepArgs a{cur, oth, scr.xs, oth, c[0] * invD, invD, (K == 1) ? 0.0 : -invD, lpr};
+    PF_CHECK(launch_ham_step(plan, dtype, a, s));
+    PF_CHECK(check_timeout(plan, s));
+    PF_CHECK(slice_out(dtype, abi, oth, g.dim, W, ncols, d_Y, n_b, col0, scr.flag, s));
+  }
+  float flag[3] = {0, 0, 0};
+  PF_CUDA(cudaMemcpyAsync(flag, scr.flag, sizeof(flag), cudaMemcpyDeviceToHost, s));
+  PF_CUDA(cudaStreamSynchronize(s));
+  int bad = 0;
+  memcpy(&bad, &flag[2], 4);
+  double csum = 0.0;
+  for (int n = 0; n <= K; n++) csum += std::fabs(c[n]);
+  const double bound = csum * invD * std::sqrt((double)g.dim) * (double)flag[0] * 1.01 + 1e-300;
+  if (bad || (double)flag[1] > bound)
+    return fail(POLFED_EBOUNDS, "filter output grew beyond the Chebyshev bound: spectrum outside [e_lo, e_hi]");
+  return POLFED_OK;
+}
+
+}  // namespace polfed
+
+extern "C" int polfed_cheb_filter_static(const polfed_model* model, const uint32_t* d_states, int64_t dim,
+                                         double e_lo, double e_hi, double sigma, int32_t K, const double* coeffs,
+                                         const void* d_X, void* d_Y, int32_t n_b, int32_t dtype,
+                                         polfed_stream_t stream) {
+  using namespace polfed;
+  if (!model) return fail(POLFED_EINVAL, "model is NULL");
+  if (model->L < 4 || model->L > 32 || (model->L & 1)) return fail(POLFED_EINVAL, "L must be even, 4 <= L <= 32");
+  if (dim != (int64_t)binom_host(model->L, model->L / 2)) return fail(POLFED_EINVAL, "dim != C(L, L/2)");
+  if (!d_states || !d_X || !d_Y) return fail(POLFED_EINVAL, "NULL device pointer");
+  if (n_b < 1 || n_b > 128) return fail(POLFED_EINVAL, "n_b must be in 1..128");
+  if (dtype != POLFED_F32 && dtype != POLFED_F64 && dtype != POLFED_DF64) return fail(POLFED_EINVAL, "bad dtype");
+  {
+    const size_t es = dtype == POLFED_F32 ? 4 : 8;
+    const char* x = (const char*)d_X;
+    const char* y = (const char*)d_Y;
+    const size_t nbytes = (size_t)dim * n_b * es;
+    if (x < y + nbytes && y < x + nbytes) return fail(POLFED_EINVAL, "X and Y must not overlap");
+  }
+  if (!std::isfinite(e_lo) || !std::isfinite(e_hi) || (!(e_lo == 0.0 && e_hi == 0.0) && !(e_lo < e_hi)))
+    return fail(POLFED_EINVAL, "need e_lo < e_hi (or both 0)");
+  if (K < 0 || K > 10000000) return fail(POLFED_EINVAL, "K must be in 0..1e7");
+  if (!coeffs && !(sigma > -1.0 && sigma < 1.0)) return fail(POLFED_EINVAL, "sigma must be in (-1, 1)");
+  CoefSource c{coeffs, sigma, coeffs ? 0.0 : std::acos(sigma)};
+  double invD = 1.0;
+  if (coeffs) {
+    for (int n = 0; n <= K; n++)
+      if (!std::isfinite(coeffs[n])) return fail(POLFED_EINVAL, "non-finite coefficient");
+  } else {
+    double D = 0.0;
+    for (int n = 0; n <= K; n++) D += c[n] * c.T(n);
+    invD = 1.0 / D;
+  }
+  return static_filter(model, e_lo, e_hi, c, K, invD, d_X, d_Y, n_b, dtype, (cudaStream_t)stream);
+}
