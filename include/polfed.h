@@ -72,7 +72,8 @@ typedef struct polfed_opts {
   double tol_conv;       /* block-Lanczos convergence: ||B_{j+1} t~_i|| <= tol_conv (units of P) */
   double tol_resid;      /* acceptance: ||H u - E u|| <= tol_resid * ||H||, ||H|| = max(|E_min|, |E_max|) */
   double cols_factor;    /* Lanczos column budget = cols_factor * (1 + k_margin) * N_ev (paper: 2.8) */
-  int32_t precision;     /* filter arithmetic: POLFED_F64, POLFED_F32 (+ refinement) or POLFED_DF64 */
+  int32_t precision;     /* filter arithmetic: POLFED_F64, POLFED_DF64, or POLFED_F32 for the Lanczos stage
+                            followed by float-float refinement sweeps (Jackson-damped filter + Rayleigh-Ritz) */
   int32_t bounds_steps;  /* max single-vector Lanczos steps for E_min / E_max */
   int32_t verbose;       /* 1 = progress lines on stderr */
   int32_t reserved;
@@ -87,6 +88,8 @@ typedef struct polfed_stats {
   int32_t n_conv;        /* converged Ritz pairs with theta >= p */
   int32_t n_ritz_checks; /* eigen-solves of T_j */
   int32_t status;        /* final status */
+  int32_t n_refine;      /* refinement sweeps (POLFED_F32 precision) */
+  int32_t refine_K;      /* order of the last refinement filter */
   int64_t dim;           /* N */
   int64_t matvec_cols;   /* column matrix-vector products with H~ (filter + bounds + checks) */
   double E_min, E_max;   /* spectral bounds (Lanczos) */

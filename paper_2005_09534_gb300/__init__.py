@@ -52,7 +52,8 @@ class COpts(ctypes.Structure):
 
 class CStats(ctypes.Structure):
     _fields_ = [("K", c_int32), ("m", c_int32), ("n_b", c_int32), ("n_conv", c_int32),
-                ("n_ritz_checks", c_int32), ("status", c_int32), ("dim", c_int64), ("matvec_cols", c_int64),
+                ("n_ritz_checks", c_int32), ("status", c_int32), ("n_refine", c_int32), ("refine_K", c_int32),
+                ("dim", c_int64), ("matvec_cols", c_int64),
                 ("E_min", c_double), ("E_max", c_double), ("e_lo", c_double), ("e_hi", c_double),
                 ("sigma", c_double), ("target", c_double), ("rho_sigma", c_double), ("max_resid", c_double),
                 ("t_bounds", c_double), ("t_filter", c_double), ("t_reorth", c_double), ("t_qr", c_double),

@@ -192,12 +192,13 @@ struct LanczosParams {
   polfed_opts o;
   double tol_resid_t;  // acceptance threshold on ||H~ u - eps u||
   bool accept_any;     // accept the first verified set (FP32 stage before refinement)
+  bool fill_panels;    // top the converged set up to whole panels (input of the refinement)
 };
 
 struct LanczosOut {
   std::vector<double> evals_t;  // H~ units, ascending
   std::vector<double> resid_t;  // H~ units
-  int n_out = 0, m = 0, n_conv = 0, checks = 0;
+  int n_out = 0, m = 0, n_conv = 0, checks = 0, ritz_cols = 0, n_refine = 0, refine_K = 0;
   int64_t matvec_cols = 0;
   double t_filter = 0, t_reorth = 0, t_qr = 0, t_teig = 0, t_ritz = 0;
 };
@@ -412,47 +413,25 @@ int run_lanczos(polfed_ctx* c, HamPlan& plan, const LanczosParams& P, double* d_
 // Ritz vectors of the converged pairs (theta >= p - 0.02, ||B t~|| <= tol_sel),
 // Rayleigh-Ritz with H~ on their span, the N_ev pairs nearest sigma, residuals.
 // The Lanczos basis is left intact (outputs live in the ritz buffer).
-int extract(polfed_ctx* c, HamPlan& plan, const LanczosParams& P, const double* Qb, int m_done,
-            const std::vector<double>& theta, const std::vector<double>& tres, double tol_sel, double* d_evecs,
-            LanczosOut& out) {
+// Rayleigh-Ritz with H~ on the span of the nr (orthonormal) columns of U
+// (panel-major, ncols padded to panels with zero columns), the N_ev pairs
+// nearest sigma, their residual norms ||H~ u - eps u|| (text after Eq. (4)).
+// Uses the Wr/Uo/Wo regions of the ritz buffer; writes out.* and d_evecs.
+int rr_select(polfed_ctx* c, HamPlan& plan, const LanczosParams& P, const double* U, int nr, double* d_evecs,
+              LanczosOut& out) {
   cudaStream_t s = c->stream;
   Dense& D = c->dense;
   const int64_t dim = plan.geo.dim;
   const int S = P.S;
   const int64_t pstride = dim * S;
-  const int n = m_done * S;
-  const double p_rr = P.o.p - 0.02;
-  std::vector<int> conv_idx;
-  for (int i = 0; i < n; i++)
-    if (theta[i] >= p_rr && tres[i] <= tol_sel) conv_idx.push_back(i);
-  if (conv_idx.empty()) {
-    out.n_out = 0;
-    out.evals_t.clear();
-    out.resid_t.clear();
-    return POLFED_OK;
-  }
-  const int nr = (int)conv_idx.size();
   const int npan = (nr + S - 1) / S;
   const int nr_pad = npan * S;
   const int nout = std::min(nr, P.N_ev);
   const int opan = (nout + S - 1) / S;
-  // T eigenvectors are in c->evbuf (column-major n x n)
-  double* Td = c->evbuf.as<double>();
-  PF_CHECK(c->vecs.ensure(((size_t)n * nr_pad + 64) * sizeof(double) + (size_t)nr_pad * sizeof(int), &c->ws_total,
-                          c->ws_limit));
-  double* Vsel = c->vecs.as<double>();
-  int* idx_d = (int*)(Vsel + (size_t)n * nr_pad + 64);
-  PF_CUDA(cudaMemcpyAsync(idx_d, conv_idx.data(), nr * sizeof(int), cudaMemcpyHostToDevice, s));
-  k_gather_cols<<<1024, 256, 0, s>>>(Td, n, idx_d, nr, n, Vsel, n);
-  PF_CUDA(cudaGetLastError());
-  count_launch();
-  PF_CHECK(c->ritz.ensure((size_t)(2 * nr_pad + 2 * opan * S) * dim * sizeof(double), &c->ws_total, c->ws_limit));
-  double* Ur = c->ritz.as<double>();          // nr_pad columns, panel-major
-  double* Wr = Ur + (size_t)nr_pad * dim;      // H~ Ur
-  double* Uo = Wr + (size_t)nr_pad * dim;      // selected eigenvectors
-  double* Wo = Uo + (size_t)opan * pstride;    // their images
-  PF_CHECK(D.update(Qb, pstride, m_done, Vsel, 1, n, nr, Ur, pstride, 1.0, 0.0, s));
-  // W = H~ U in FP64, panel by panel
+  double* base = c->ritz.as<double>();
+  double* Wr = base + (size_t)nr_pad * dim;   // H~ U
+  double* Uo = Wr + (size_t)nr_pad * dim;     // selected eigenvectors
+  double* Wo = Uo + (size_t)opan * pstride;   // their images
   PF_CHECK(plan.prepare_typed(POLFED_F64, P.e_lo, P.e_hi));
   const int lpr64 = choose_lpr(POLFED_F64, S);
   PF_CHECK(c->fscr.ensure(std::max(c->fscr.n, filter_scratch_bytes(plan, POLFED_F64, lpr64)), &c->ws_total,
@@ -461,14 +440,14 @@ int extract(polfed_ctx* c, HamPlan& plan, const LanczosParams& P, const double* 
   scr64.xs = c->fscr.p;
   scr64.bytes = c->fscr.n;
   for (int q = 0; q < npan; q++)
-    PF_CHECK(apply_block(plan, POLFED_F64, Ur + (size_t)q * pstride, Wr + (size_t)q * pstride, S, POLFED_F64, scr64, s,
+    PF_CHECK(apply_block(plan, POLFED_F64, U + (size_t)q * pstride, Wr + (size_t)q * pstride, S, POLFED_F64, scr64, s,
                          lpr64));
   out.matvec_cols += nr_pad;
   // G = U^T W (nr_pad x nr_pad); the eigen-solve of its leading nr x nr block
   PF_CHECK(c->evbuf.ensure(((size_t)nr_pad * nr_pad + nr_pad) * sizeof(double), &c->ws_total, c->ws_limit));
   double* G = c->evbuf.as<double>();
   double* lam = G + (size_t)nr_pad * nr_pad;
-  for (int q = 0; q < npan; q++) PF_CHECK(D.gram(Ur, pstride, npan, Wr + (size_t)q * pstride, G, nr_pad, q * S, s));
+  for (int q = 0; q < npan; q++) PF_CHECK(D.gram(U, pstride, npan, Wr + (size_t)q * pstride, G, nr_pad, q * S, s));
   PF_CHECK(syevd(c, G, nr, nr_pad, lam));
   std::vector<double> lamh(nr);
   PF_CUDA(cudaMemcpyAsync(lamh.data(), lam, nr * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -480,14 +459,18 @@ int extract(polfed_ctx* c, HamPlan& plan, const LanczosParams& P, const double* 
                    [&](int x, int y) { return std::fabs(lamh[x] - P.sigma) < std::fabs(lamh[y] - P.sigma); });
   sel.resize(nout);
   std::sort(sel.begin(), sel.end());
+  PF_CHECK(c->vecs.ensure(((size_t)nr_pad * nout + 64) * sizeof(double) + (size_t)nr_pad * sizeof(int), &c->ws_total,
+                          c->ws_limit));
+  double* Ysel = c->vecs.as<double>();
+  int* idx_d = (int*)(Ysel + (size_t)nr_pad * nout + 64);
   PF_CUDA(cudaMemcpyAsync(idx_d, sel.data(), nout * sizeof(int), cudaMemcpyHostToDevice, s));
-  // rows nr..nr_pad-1 multiply the zero padding columns of Ur/Wr: make them 0, not stale memory
-  PF_CUDA(cudaMemsetAsync(Vsel, 0, (size_t)nr_pad * nout * sizeof(double), s));
-  k_gather_cols<<<1024, 256, 0, s>>>(G, nr_pad, idx_d, nout, nr, Vsel, nr_pad);
+  // rows nr..nr_pad-1 multiply the zero padding columns of U/W: make them 0, not stale memory
+  PF_CUDA(cudaMemsetAsync(Ysel, 0, (size_t)nr_pad * nout * sizeof(double), s));
+  k_gather_cols<<<1024, 256, 0, s>>>(G, nr_pad, idx_d, nout, nr, Ysel, nr_pad);
   PF_CUDA(cudaGetLastError());
   count_launch();
-  PF_CHECK(D.update(Ur, pstride, npan, Vsel, 1, nr_pad, nout, Uo, pstride, 1.0, 0.0, s));
-  PF_CHECK(D.update(Wr, pstride, npan, Vsel, 1, nr_pad, nout, Wo, pstride, 1.0, 0.0, s));
+  PF_CHECK(D.update(U, pstride, npan, Ysel, 1, nr_pad, nout, Uo, pstride, 1.0, 0.0, s));
+  PF_CHECK(D.update(Wr, pstride, npan, Ysel, 1, nr_pad, nout, Wo, pstride, 1.0, 0.0, s));
   std::vector<double> lsel(opan * S, 0.0);
   for (int i = 0; i < nout; i++) lsel[i] = lamh[sel[i]];
   double* lsel_d = lam;  // reuse
@@ -505,6 +488,133 @@ int extract(polfed_ctx* c, HamPlan& plan, const LanczosParams& P, const double* 
   PF_CUDA(cudaStreamSynchronize(s));
   out.n_out = nout;
   return POLFED_OK;
+}
+
+// Room in the ritz buffer for U, H~U, the selected pairs and a filtered copy of U.
+int ensure_ritz(polfed_ctx* c, int64_t dim, int S, int nr, int N_ev) {
+  const int nr_pad = ((nr + S - 1) / S) * S;
+  const int opan = (std::min(nr, N_ev) + S - 1) / S;
+  return c->ritz.ensure((size_t)(3 * nr_pad + 2 * opan * S) * dim * sizeof(double), &c->ws_total, c->ws_limit);
+}
+
+// Ritz vectors u_i = Q_m t_i of the converged pairs (theta >= p - 0.02,
+// ||B t~|| <= tol_sel), then rr_select.  With fill_panels the set is topped up
+// with the next Ritz vectors by theta to whole panels (a full-rank block for
+// the refinement sweeps).  The Lanczos basis is left intact.
+int extract(polfed_ctx* c, HamPlan& plan, const LanczosParams& P, const double* Qb, int m_done,
+            const std::vector<double>& theta, const std::vector<double>& tres, double tol_sel, double* d_evecs,
+            LanczosOut& out) {
+  cudaStream_t s = c->stream;
+  Dense& D = c->dense;
+  const int64_t dim = plan.geo.dim;
+  const int S = P.S;
+  const int64_t pstride = dim * S;
+  const int n = m_done * S;
+  const double p_rr = P.o.p - 0.02;
+  std::vector<int> conv_idx;
+  std::vector<char> used(n, 0);
+  for (int i = 0; i < n; i++)
+    if (theta[i] >= p_rr && tres[i] <= tol_sel) {
+      conv_idx.push_back(i);
+      used[i] = 1;
+    }
+  if (conv_idx.empty()) {
+    out.n_out = 0;
+    out.evals_t.clear();
+    out.resid_t.clear();
+    return POLFED_OK;
+  }
+  if (P.fill_panels) {
+    std::vector<int> rest;
+    for (int i = 0; i < n; i++)
+      if (!used[i]) rest.push_back(i);
+    std::sort(rest.begin(), rest.end(), [&](int x, int y) { return theta[x] > theta[y]; });
+    size_t k = 0;
+    while (conv_idx.size() % S && k < rest.size()) conv_idx.push_back(rest[k++]);
+  }
+  const int nr = (int)conv_idx.size();
+  const int npan = (nr + S - 1) / S;
+  // T eigenvectors are in c->evbuf (column-major n x n)
+  double* Td = c->evbuf.as<double>();
+  PF_CHECK(c->vecs.ensure(((size_t)n * npan * S + 64) * sizeof(double) + (size_t)npan * S * sizeof(int), &c->ws_total,
+                          c->ws_limit));
+  double* Vsel = c->vecs.as<double>();
+  int* idx_d = (int*)(Vsel + (size_t)n * npan * S + 64);
+  PF_CUDA(cudaMemcpyAsync(idx_d, conv_idx.data(), nr * sizeof(int), cudaMemcpyHostToDevice, s));
+  k_gather_cols<<<1024, 256, 0, s>>>(Td, n, idx_d, nr, n, Vsel, n);
+  PF_CUDA(cudaGetLastError());
+  count_launch();
+  PF_CHECK(ensure_ritz(c, dim, S, nr, P.N_ev));
+  double* Ur = c->ritz.as<double>();  // npan panels
+  PF_CHECK(D.update(Qb, pstride, m_done, Vsel, 1, n, nr, Ur, pstride, 1.0, 0.0, s));
+  out.ritz_cols = nr;
+  return rr_select(c, plan, P, Ur, nr, d_evecs, out);
+}
+
+// Jackson damping factors g_n of an order-N Chebyshev expansion (kernel
+// polynomial method; Weisse, Wellein, Alvermann, Fehske, Rev. Mod. Phys. 78,
+// 275 (2006), Eq. (71)).
+static void jackson(int N, std::vector<double>& g) {
+  g.resize(N + 1);
+  const double a = M_PI / (N + 1);
+  for (int n = 0; n <= N; n++) g[n] = ((N - n + 1) * std::cos(a * n) + std::sin(a * n) / std::tan(a)) / (N + 1);
+}
+
+// One refinement sweep (mixed precision): W = Pj(H~) U with the Jackson-damped
+// order-Kr transform of Eq. (2) in float-float arithmetic, W orthonormalized
+// (block Gram-Schmidt twice + Cholesky QR twice per panel), then rr_select on
+// span(W).  U holds nr orthonormal columns in panels (ritz buffer region 0);
+// the padding columns of the last panel are exactly zero and stay zero through
+// the filter, the Gram-Schmidt and the Cholesky QR.  On return region 0 holds W.
+int refine(polfed_ctx* c, HamPlan& plan, const LanczosParams& P, int Kr, int nr, double* d_evecs, LanczosOut& out) {
+  cudaStream_t s = c->stream;
+  Dense& D = c->dense;
+  const int64_t dim = plan.geo.dim;
+  const int S = P.S;
+  const int64_t pstride = dim * S;
+  const int npan = (nr + S - 1) / S;
+  const int opan = (std::min(nr, P.N_ev) + S - 1) / S;
+  PF_CHECK(ensure_ritz(c, dim, S, nr, P.N_ev));
+  double* U = c->ritz.as<double>();
+  double* F = U + (size_t)(2 * npan + 2 * opan) * pstride;  // after U, Wr, Uo, Wo
+  std::vector<double> cf, g;
+  double Dn = 1.0;
+  cheb_coeffs(P.sigma, Kr, cf, Dn);
+  jackson(Kr, g);
+  for (int n = 0; n <= Kr; n++) cf[n] *= g[n] / Dn;
+  PF_CHECK(plan.prepare_typed(POLFED_DF64, P.e_lo, P.e_hi));
+  const int lpr = choose_lpr(POLFED_DF64, S);
+  PF_CHECK(c->fscr.ensure(std::max(c->fscr.n, filter_scratch_bytes(plan, POLFED_DF64, lpr)), &c->ws_total,
+                          c->ws_limit));
+  FilterScratch scr;
+  scr.xs = c->fscr.p;
+  scr.bytes = c->fscr.n;
+  const double t0 = now_s();
+  for (int q = 0; q < npan; q++)
+    PF_CHECK(filter_block(plan, POLFED_DF64, cf.data(), Kr, 1.0, U + (size_t)q * pstride, F + (size_t)q * pstride, S,
+                          POLFED_F64, scr, s, lpr));
+  out.matvec_cols += (int64_t)Kr * nr;
+  const double t1 = now_s();
+  out.t_filter += t1 - t0;
+  // orthonormalize F panel by panel
+  PF_CHECK(c->small.ensure(std::max(c->small.n, ((size_t)npan * S * S + 16) * sizeof(double)), &c->ws_total,
+                           c->ws_limit));
+  double* Cd = c->small.as<double>();
+  bool brk = false;
+  for (int q = 0; q < npan; q++) {
+    double* Fq = F + (size_t)q * pstride;
+    for (int pass = 0; pass < 2 && q > 0; pass++) {
+      PF_CHECK(D.gram(F, pstride, q, Fq, Cd, S, 0, s));
+      PF_CHECK(D.update(F, pstride, q, Cd, S, 1, S, Fq, 0, -1.0, 1.0, s));
+    }
+    PF_CHECK(D.cholqr(Fq, Fq, nullptr, 2, s, &brk));
+    const bool padded = (q == npan - 1) && (nr % S != 0);  // zero columns trip the pivot test by design
+    if (brk && !padded) return fail(POLFED_ENOCONV, "refinement block lost rank");
+  }
+  out.t_reorth += now_s() - t1;
+  // region 0 <- F, then Rayleigh-Ritz on it
+  PF_CUDA(cudaMemcpyAsync(U, F, (size_t)npan * pstride * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  return rr_select(c, plan, P, U, nr, d_evecs, out);
 }
 
 // Single-vector Lanczos on H for E_min and E_max (text before Eq. (3)).
@@ -676,7 +786,7 @@ int polfed_block_lanczos(polfed_ctx* c, const polfed_model* model, double e_lo, 
   PF_CHECK(plan.init(model, c->stream, false));
   const double hn = std::max(std::fabs(e_lo), std::fabs(e_hi));
   LanczosParams P{e_lo, e_hi, sigma, K, round_block(n_b), N_ev, c->opts, c->opts.tol_resid * hn / (0.5 * (e_hi - e_lo)),
-                  false};
+                  false, false};
   LanczosOut o;
   const double t0 = now_s();
   int rc = run_lanczos(c, plan, P, d_evecs, o);
@@ -768,10 +878,35 @@ int polfed_eigs(polfed_ctx* c, const polfed_model* model, double eps_target, int
   // 3. block Lanczos
   const int S = round_block(n_b);
   const double hnorm0 = std::max(std::fabs(Emin), std::fabs(Emax));
-  LanczosParams P{e_lo, e_hi, sigma, K, S, N_ev, o, o.tol_resid * hnorm0 / (0.5 * (e_hi - e_lo)), false};
+  const bool mixed = o.precision == POLFED_F32;
+  LanczosParams P{e_lo, e_hi, sigma, K, S, N_ev, o, o.tol_resid * hnorm0 / (0.5 * (e_hi - e_lo)), mixed, false};
+  if (mixed) P.o.tol_conv = std::max(o.tol_conv, 2e-5);  // FP32 filter: stop at its noise floor
   LanczosOut lo;
   int rc = run_lanczos(c, plan, P, d_evecs, lo);
   if (rc != POLFED_OK && rc != POLFED_ENOCONV) return rc;
+  if (mixed && lo.n_out > 0) {
+    // refinement sweeps with a float-float filter until the residuals pass
+    int Kr = std::max(16, K / 2);
+    if (sigma == 0.0) Kr &= ~1;
+    for (int sweep = 0; sweep < 3; sweep++) {
+      double mr = 0.0;
+      for (double r : lo.resid_t) mr = std::max(mr, r);
+      if (lo.n_out >= N_ev && mr <= P.tol_resid_t && sweep > 0) break;
+      if (o.verbose || debug_on())
+        fprintf(stderr, "[polfed] refinement sweep %d: Kr %d, max resid (H~) before %.3e\n", sweep + 1, Kr, mr);
+      const double tr0 = now_s();
+      const int rrc = refine(c, plan, P, Kr, lo.ritz_cols, d_evecs, lo);
+      lo.t_ritz += now_s() - tr0;
+      if (rrc != POLFED_OK) return rrc;
+      lo.n_refine++;
+      lo.refine_K = Kr;
+      Kr = std::min(2 * Kr, K);
+    }
+    double mr = 0.0;
+    for (double r : lo.resid_t) mr = std::max(mr, r);
+    rc = (lo.n_out >= N_ev && mr <= P.tol_resid_t) ? POLFED_OK
+                                                   : fail(POLFED_ENOCONV, "refinement did not reach the residual target");
+  }
   const double half = 0.5 * (e_hi - e_lo), mid = 0.5 * (e_hi + e_lo);
   const double hnorm = std::max(std::fabs(Emin), std::fabs(Emax));
   polfed_stats st;
@@ -788,6 +923,8 @@ int polfed_eigs(polfed_ctx* c, const polfed_model* model, double eps_target, int
   st.n_conv = lo.n_conv;
   st.n_ritz_checks = lo.checks;
   st.status = rc;
+  st.n_refine = lo.n_refine;
+  st.refine_K = lo.refine_K;
   st.dim = dim;
   st.matvec_cols = lo.matvec_cols + mv;
   st.E_min = Emin;

@@ -57,4 +57,4 @@ def test_struct_layouts_match_header():
     # polfed_model: int32, int32, 3 doubles, pointer; opts: 5 doubles, 4 int32, uint64
     assert ctypes.sizeof(pf.CModel) == 8 + 24 + 8
     assert ctypes.sizeof(pf.COpts) == 40 + 16 + 8
-    assert ctypes.sizeof(pf.CStats) == 6 * 4 + 2 * 8 + 15 * 8 + 2 * 8 + 2 * 8
+    assert ctypes.sizeof(pf.CStats) == 8 * 4 + 2 * 8 + 15 * 8 + 2 * 8 + 2 * 8
