@@ -76,9 +76,24 @@ typedef struct polfed_opts {
                             followed by float-float refinement sweeps (Jackson-damped filter + Rayleigh-Ritz) */
   int32_t bounds_steps;  /* max single-vector Lanczos steps for E_min / E_max */
   int32_t verbose;       /* 1 = progress lines on stderr */
-  int32_t reserved;
-  uint64_t seed;         /* seed of the random starting block Q_1 */
+  int32_t dos_rule;      /* how K gets the density of states at the target: POLFED_DOS_* */
+  uint64_t seed;         /* seed of the random starting block Q_1 (and of the KPM vectors) */
+  double rho_hint;       /* POLFED_DOS_HINT: (E_max - E_min) rho(E*) / N, the density of states at the target per
+                            unit of rescaled energy eps, per state (e.g. from polfed_mlp_predict) */
+  double emin_hint, emax_hint; /* POLFED_DOS_HINT: predicted, padded spectral bounds; used as [e_lo, e_hi] when the
+                            Lanczos probe confirms that they contain the spectrum, else ignored (0, 0 = none) */
+  int32_t kpm_moments;   /* POLFED_DOS_KPM: Chebyshev moments (default 256) */
+  int32_t kpm_vectors;   /* POLFED_DOS_KPM: random vectors of the stochastic trace (default 16) */
 } polfed_opts;
+
+/* Density-of-states rules for the choice of K (polfed_opts.dos_rule). */
+enum {
+  POLFED_DOS_MOMENTS = 0, /* Gaussian with the exact sector mean and variance of H (Tr H / N, Tr H^2 / N) */
+  POLFED_DOS_GAMMA = 1,   /* the paper's analytic width: Gamma^2 = L [(J1^2 + J2^2)/8 + Delta^2 (J1^2 + J2^2)/16
+                             + sum_i h_i^2 / (4L)], centred at the sector mean */
+  POLFED_DOS_KPM = 2,     /* stochastic kernel-polynomial estimate at the target (polfed_kpm_moments) */
+  POLFED_DOS_HINT = 3     /* the caller's rho_hint (and bounds hints), e.g. from the learned predictor */
+};
 
 /* Counters and timers of one polfed_eigs / polfed_block_lanczos call. */
 typedef struct polfed_stats {
@@ -103,12 +118,17 @@ typedef struct polfed_stats {
   int64_t n_step_launches; /* launches of the Chebyshev / H~ step kernel */
   double step_gpu_s;       /* device time of those launches (CUDA events on the launching stream) */
   double step_alg_bytes;   /* algorithmic bytes of those launches: N * cols * w * (3 + [c_k != 0]) each */
+  int32_t dos_rule;        /* rule that set K */
+  int32_t bounds_from_hint;/* 1 if [e_lo, e_hi] came from the caller's (probe-confirmed) bounds hints */
+  int32_t n_restarts;      /* restarts with a smaller K because fewer than N_ev eigenvalues had P >= p */
+  int32_t reserved;
 } polfed_stats;
 
 typedef struct polfed_ctx polfed_ctx;
 
 /* Default options: p = 0.17, k_margin = 0.2, tol_conv = 1e-7 (tightened until the residuals pass), tol_resid = 1e-8,
- * cols_factor = 2.8, precision = POLFED_DF64, bounds_steps = 600, seed = 1234. */
+ * cols_factor = 2.8, precision = POLFED_DF64, bounds_steps = 600, dos_rule = POLFED_DOS_MOMENTS, seed = 1234,
+ * no hints, kpm_moments = 256, kpm_vectors = 16. */
 void polfed_opts_default(polfed_opts* opts);
 
 /* Basis of the S^z sector with n_up up spins ("Benchmark models": N = C(L, L/2)
@@ -219,10 +239,171 @@ int polfed_block_lanczos(polfed_ctx* ctx, const polfed_model* model, double e_lo
  *   d_evecs    : device out, dim x N_ev column-major FP64, or NULL.
  *   resid      : host out, N_ev residual norms (H units), or NULL.
  *   stats      : host out or NULL.
+ * With K = 0, a run that finds fewer than N_ev Ritz values with P >= p (the
+ * density of states was overestimated) restarts, at most twice, with a
+ * smaller K.  With precision POLFED_F32 the FP32-stage pairs are refined by
+ * up to six float-float filter + Rayleigh-Ritz sweeps.
  * Blocking.  Returns POLFED_ENOCONV with partial results if the column
  * budget ran out. */
 int polfed_eigs(polfed_ctx* ctx, const polfed_model* model, double eps_target, int32_t N_ev, int32_t K, int32_t n_b,
                 const polfed_opts* opts, double* evals, double* d_evecs, double* resid, polfed_stats* stats);
+
+/* Spectral bounds E_min, E_max of H by single-vector Lanczos (the first step
+ * of the "POLFED algorithm" section): stops when both extreme Ritz values have
+ * residual bounds |beta_m t_m| <= 1e-12 max(|E_min|, |E_max|) or after
+ * opts.bounds_steps steps (opts of the last polfed_eigs call on ctx, else
+ * defaults).
+ *   bounds : host out, {E_min, E_max, err} with err the larger residual bound.
+ * Blocking. */
+int polfed_spectral_bounds(polfed_ctx* ctx, const polfed_model* model, double* bounds);
+
+/* Stochastic Chebyshev moments of H~ (kernel polynomial method; the paper
+ * cites such estimators for the density of states that fixes K):
+ *   mu[n] = (1/R) sum_{r<R} x_r^T T_n(H~) x_r,  n = 0..n_mom-1,
+ * with x_r the columns of d_R.  E[mu_n] = Tr T_n(H~) when the entries of x_r
+ * are independent with zero mean and unit variance.
+ *   e_lo, e_hi : rescaling interval (must contain the spectrum).
+ *   n_mom      : 2 <= n_mom <= 65536; takes ceil(n_mom / 2) applications of H~
+ *                (T_{2k} = 2 T_k^2 - T_0, T_{2k+1} = 2 T_{k+1} T_k - T_1).
+ *   d_R        : device, row-major dim x R (float for POLFED_F32, else double), read only.
+ *   R          : 1..128.
+ *   dtype      : arithmetic of the H~ applications (POLFED_F64 / DF64 / F32).
+ *   mu         : host out, n_mom doubles.
+ * Synchronizes the stream.  POLFED_EBOUNDS if some |mu_n| > 1.01 mu_0
+ * (spectrum outside [e_lo, e_hi]). */
+int polfed_kpm_moments(const polfed_model* model, const uint32_t* d_states, int64_t dim, double e_lo, double e_hi,
+                       int32_t n_mom, const void* d_R, int32_t R, int32_t dtype, double* mu, polfed_stream_t stream);
+
+/* Fraction of the spectrum of H~ inside [x_a, x_b] (-1 <= x_a <= x_b <= 1)
+ * from KPM moments: sum_n g_n c_n mu_n / mu_0 with Jackson factors g_n (Weisse
+ * et al., Rev. Mod. Phys. 78, 275, Eq. (71), N = n_mom) and the indicator's
+ * Chebyshev coefficients c_0 = (th_a - th_b)/pi, c_n = 2 (sin n th_a - sin n th_b)/(n pi),
+ * th = arccos x.  Host only. */
+int polfed_kpm_count(const double* mu, int32_t n_mom, double x_a, double x_b, double* fraction);
+
+/* Labels for the learned predictor, produced by the method's own machinery:
+ * out[0] = E_min, out[1] = E_max (polfed_spectral_bounds), out[2] = the
+ * density of states at E* = E_min + eps_target (E_max - E_min) per unit of
+ * eps and per state, (E_max - E_min) rho(E*) / N, from the KPM eigenvalue
+ * count of a window around E* (n_mom moments, R random vectors seeded by
+ * opts.seed).  Blocking. */
+int polfed_spectral_labels(polfed_ctx* ctx, const polfed_model* model, double eps_target, int32_t n_mom, int32_t R,
+                           double* out);
+
+/* ------------------------------------------------------------------------
+ * Learned predictor of the spectral bounds and of the density of states
+ * (the paper has no counterpart: it takes E_min / E_max from Lanczos and
+ * rho from a Gaussian estimate).  A fully connected FP32 network
+ * x -> tanh(W1 x + b1) -> tanh(W2 . + b2) -> W3 . + b3, trained and evaluated
+ * by this library's kernels.  Parameters are one float array:
+ * W1 [H x d_in] row-major, b1 [H], W2 [H x H], b2 [H], W3 [d_out x H], b3 [d_out].
+ * Inputs and targets are standardized inside the network with the affine
+ * maps set by polfed_mlp_set_scaling (identity by default):
+ * x' = (x - x_mean) / x_std, and the network's outputs are in units of
+ * (y - y_mean) / y_std.  All device arrays are row-major B x d.
+ * ------------------------------------------------------------------------ */
+typedef struct polfed_mlp polfed_mlp;
+
+/* d_in 1..1024, hidden d_out..4096, d_out 1..64; weights uniform in
+ * +-sqrt(6 / (fan_in + fan_out)) from a splitmix64 stream of seed, biases 0.
+ * The network lives on the current device. */
+int polfed_mlp_create(int32_t d_in, int32_t hidden, int32_t d_out, uint64_t seed, polfed_mlp** out);
+void polfed_mlp_destroy(polfed_mlp* net);
+int32_t polfed_mlp_num_params(const polfed_mlp* net);
+/* Host copies of the parameters (set also resets the Adam state). */
+int polfed_mlp_set_params(polfed_mlp* net, const float* host);
+int polfed_mlp_get_params(const polfed_mlp* net, float* host);
+/* Host arrays of d_in (x) and d_out (y) floats; std entries must be > 0. */
+int polfed_mlp_set_scaling(polfed_mlp* net, const float* x_mean, const float* x_std, const float* y_mean,
+                           const float* y_std);
+/* d_y = network(d_x) in target units (de-standardized); B >= 1.  Synchronizes the stream. */
+int polfed_mlp_forward(polfed_mlp* net, const float* d_x, int32_t B, float* d_y, polfed_stream_t stream);
+/* Gradient of the loss 0.5/B sum_b |f(x_b) - t'_b|^2 (t' = standardized targets)
+ * with respect to the parameters; d_grad (device, num_params floats) may be
+ * NULL; loss (host) may be NULL.  Synchronizes the stream. */
+int polfed_mlp_grad(polfed_mlp* net, const float* d_x, const float* d_t, int32_t B, float* d_grad, float* loss,
+                    polfed_stream_t stream);
+/* One Adam step (Kingma & Ba; beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected)
+ * on the gradient above with learning rate lr.  Synchronizes the stream. */
+int polfed_mlp_train_step(polfed_mlp* net, const float* d_x, const float* d_t, int32_t B, float lr, float* loss,
+                          polfed_stream_t stream);
+/* Feature and target conventions of the spectral predictor (d_in = L + 1, d_out = 3):
+ *   x = (h_0, ..., h_{L-1}, W)   (W: the disorder strength the fields were drawn with)
+ *   y = (E_min / L, E_max / L, log rho_eps), rho_eps = (E_max - E_min) rho(E*) / N.
+ * polfed_mlp_features writes x (host, L + 1 floats); polfed_mlp_targets maps
+ * labels {E_min, E_max, rho_eps} (host) of a chain of length L to y (host, 3 floats). */
+int polfed_mlp_features(const polfed_model* model, double W, float* x);
+int polfed_mlp_targets(int32_t L, const double* labels, float* y);
+/* Prediction for one realization: out = {E_min, E_max, rho_eps} (host), i.e.
+ * the inverse of polfed_mlp_targets applied to the network's output for
+ * polfed_mlp_features(model, W).  Needs d_in == L + 1 and d_out == 3.  Blocking. */
+int polfed_mlp_predict(polfed_mlp* net, const polfed_model* model, double W, double* out);
+
+/* ------------------------------------------------------------------------
+ * Batched runner (the paper runs disorder realizations independently, one
+ * per compute node; this is the single-GPU form of that parallelism).
+ * ------------------------------------------------------------------------ */
+
+/* Eq. (2) filter of many realizations in ONE cooperative kernel launch: every
+ * (realization, 128-byte column slice) job runs its own Clenshaw recurrence of
+ * order K[i] with the paper's coefficients for sigma[i], on its own H~ (plans
+ * with the low/high split b = min(10, L - 4)).  Launch step t performs step t
+ * of every job with t < K[i]; CTAs meet at a grid barrier between steps
+ * (bounded wait: POLFED_ETIMEOUT, never a hang).
+ *   n_inst       : number of realizations (>= 1); all with J2 == 0 or all with J2 != 0.
+ *   models       : host array of n_inst models (any mix of L).
+ *   e_lo, e_hi, sigma, K : host arrays of n_inst (as in polfed_cheb_filter, K <= 1e7).
+ *   d_X, d_Y     : host arrays of n_inst device pointers, row-major dim_i x n_b
+ *                  (float for POLFED_F32, double for POLFED_DF64); X_i, Y_i must not overlap.
+ *   n_b          : 1..128 (the same for all).
+ *   dtype        : POLFED_F32 or POLFED_DF64.
+ *   ctas_per_sm  : 0 = as many as fit (1 or 2), else 1 or 2.
+ * Synchronizes the stream.  POLFED_EBOUNDS if an output grew beyond the
+ * Chebyshev bound. */
+int polfed_cheb_filter_batched(int32_t n_inst, const polfed_model* models, const double* e_lo, const double* e_hi,
+                               const double* sigma, const int32_t* K, const void* const* d_X, void* const* d_Y,
+                               int32_t n_b, int32_t dtype, int32_t ctas_per_sm, polfed_stream_t stream);
+
+/* What polfed_eigs_batched did. */
+typedef struct polfed_batch_info {
+  int32_t n_b;              /* block width of realization 0 */
+  int32_t ctas_per_sm;      /* grid of the batched filter (0 = all that fit) */
+  int32_t rounds;           /* batched filter launches */
+  int32_t workers;          /* host threads */
+  int32_t n_width16, n_width32, n_width64; /* realizations per block width */
+  int32_t reserved;
+  double t_total;           /* seconds, whole call */
+  double t_tune;            /* seconds spent autotuning */
+  double filter_gpu_s;      /* device time of the batched filter launches (CUDA events) */
+  double filter_alg_bytes;  /* their algorithmic bytes (Clenshaw minimum) */
+  double tune_step_s[3][2]; /* autotuner: seconds per filter step for widths 16/32/64 x 1/2 CTAs per SM */
+  int64_t n_launches;       /* kernels launched by the call */
+} polfed_batch_info;
+
+/* polfed_eigs for n_inst realizations at once.  Each realization runs the
+ * polfed_eigs driver on its own host thread, context and stream (at most
+ * max_workers at a time, 0 = 64); their filter calls meet and run as one
+ * polfed_cheb_filter_batched-style launch per round, while the dense block
+ * work of all realizations proceeds concurrently.
+ *   device     : CUDA device ordinal.
+ *   eps_target, N_ev, K : host arrays of n_inst (K may be NULL = all automatic).
+ *   n_b        : block width for all, or 0 = autotune: the batched filter is timed on the
+ *                realizations' operators for widths 16/32/64 and 1/2 CTAs per SM, and each
+ *                realization takes the width with the least predicted filter time.
+ *   opts       : options (precision POLFED_F32 or POLFED_DF64), or NULL.
+ *   evals      : host out, sum(N_ev) values: realization i at offset sum_{j<i} N_ev[j].
+ *   resid      : host out like evals, or NULL.
+ *   d_evecs    : host array of n_inst device pointers (dim_i x N_ev[i] column-major FP64,
+ *                each may be NULL), or NULL.
+ *   stats      : host out, n_inst, or NULL (launch and time counters of a realization
+ *                include the batched launches its thread issued for the whole round).
+ *   status     : host out, n_inst statuses.
+ *   info       : host out or NULL.
+ * Blocking.  Returns the first failing realization's status (the others still run). */
+int polfed_eigs_batched(int32_t device, int32_t n_inst, const polfed_model* models, const double* eps_target,
+                        const int32_t* N_ev, const int32_t* K, int32_t n_b, const polfed_opts* opts,
+                        int32_t max_workers, double* evals, double* resid, double* const* d_evecs,
+                        polfed_stats* stats, int32_t* status, polfed_batch_info* info);
 
 /* Message of the last failing call on this thread ("" if none). */
 const char* polfed_last_error(void);

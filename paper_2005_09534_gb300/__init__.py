@@ -10,7 +10,7 @@ from __future__ import annotations
 
 import ctypes
 import os
-from ctypes import POINTER, byref, c_double, c_int32, c_int64, c_size_t, c_uint64, c_void_p
+from ctypes import POINTER, byref, c_double, c_float, c_int32, c_int64, c_size_t, c_uint64, c_void_p
 
 import numpy as np
 
@@ -27,10 +27,16 @@ POLFED_ETIMEOUT = -6
 
 F64, F32, DF64 = 0, 1, 2
 
+DOS_MOMENTS, DOS_GAMMA, DOS_KPM, DOS_HINT = 0, 1, 2, 3
+
 EXPORTED = ["polfed_opts_default", "polfed_basis_build", "polfed_h_apply", "polfed_cheb_filter",
             "polfed_cheb_filter_static",
             "polfed_ctx_create", "polfed_ctx_destroy", "polfed_ctx_set_stream", "polfed_block_lanczos",
-            "polfed_eigs", "polfed_last_error"]
+            "polfed_eigs", "polfed_spectral_bounds", "polfed_kpm_moments", "polfed_kpm_count",
+            "polfed_spectral_labels", "polfed_mlp_create", "polfed_mlp_destroy", "polfed_mlp_num_params",
+            "polfed_mlp_set_params", "polfed_mlp_get_params", "polfed_mlp_set_scaling", "polfed_mlp_forward",
+            "polfed_mlp_grad", "polfed_mlp_train_step", "polfed_mlp_features", "polfed_mlp_targets",
+            "polfed_mlp_predict", "polfed_cheb_filter_batched", "polfed_eigs_batched", "polfed_last_error"]
 
 
 class PolfedError(RuntimeError):
@@ -47,7 +53,9 @@ class CModel(ctypes.Structure):
 class COpts(ctypes.Structure):
     _fields_ = [("p", c_double), ("k_margin", c_double), ("tol_conv", c_double), ("tol_resid", c_double),
                 ("cols_factor", c_double), ("precision", c_int32), ("bounds_steps", c_int32),
-                ("verbose", c_int32), ("reserved", c_int32), ("seed", c_uint64)]
+                ("verbose", c_int32), ("dos_rule", c_int32), ("seed", c_uint64), ("rho_hint", c_double),
+                ("emin_hint", c_double), ("emax_hint", c_double), ("kpm_moments", c_int32),
+                ("kpm_vectors", c_int32)]
 
 
 class CStats(ctypes.Structure):
@@ -59,10 +67,23 @@ class CStats(ctypes.Structure):
                 ("t_bounds", c_double), ("t_filter", c_double), ("t_reorth", c_double), ("t_qr", c_double),
                 ("t_teig", c_double), ("t_ritz", c_double), ("t_total", c_double),
                 ("n_launches", c_int64), ("n_step_launches", c_int64), ("step_gpu_s", c_double),
-                ("step_alg_bytes", c_double)]
+                ("step_alg_bytes", c_double), ("dos_rule", c_int32), ("bounds_from_hint", c_int32),
+                ("n_restarts", c_int32), ("reserved", c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class CBatchInfo(ctypes.Structure):
+    _fields_ = [("n_b", c_int32), ("ctas_per_sm", c_int32), ("rounds", c_int32), ("workers", c_int32),
+                ("n_width16", c_int32), ("n_width32", c_int32), ("n_width64", c_int32), ("reserved", c_int32),
+                ("t_total", c_double), ("t_tune", c_double), ("filter_gpu_s", c_double),
+                ("filter_alg_bytes", c_double), ("tune_step_s", c_double * 6), ("n_launches", c_int64)]
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f != "tune_step_s"}
+        d["tune_step_s"] = [[self.tune_step_s[2 * w + c] for c in range(2)] for w in range(3)]
+        return d
 
 
 _lib = None
@@ -93,6 +114,31 @@ def load(path: str = LIB_PATH):
                                          c_int32, c_void_p, POINTER(c_double), POINTER(c_double), POINTER(c_int32)]
     lib.polfed_eigs.argtypes = [c_void_p, POINTER(CModel), c_double, c_int32, c_int32, c_int32, POINTER(COpts),
                                 POINTER(c_double), c_void_p, POINTER(c_double), POINTER(CStats)]
+    lib.polfed_spectral_bounds.argtypes = [c_void_p, POINTER(CModel), POINTER(c_double)]
+    lib.polfed_kpm_moments.argtypes = [POINTER(CModel), c_void_p, c_int64, c_double, c_double, c_int32, c_void_p,
+                                       c_int32, c_int32, POINTER(c_double), c_void_p]
+    lib.polfed_kpm_count.argtypes = [POINTER(c_double), c_int32, c_double, c_double, POINTER(c_double)]
+    lib.polfed_spectral_labels.argtypes = [c_void_p, POINTER(CModel), c_double, c_int32, c_int32, POINTER(c_double)]
+    lib.polfed_mlp_create.argtypes = [c_int32, c_int32, c_int32, c_uint64, POINTER(c_void_p)]
+    lib.polfed_mlp_destroy.argtypes = [c_void_p]
+    lib.polfed_mlp_destroy.restype = None
+    lib.polfed_mlp_num_params.argtypes = [c_void_p]
+    lib.polfed_mlp_set_params.argtypes = [c_void_p, POINTER(c_float)]
+    lib.polfed_mlp_get_params.argtypes = [c_void_p, POINTER(c_float)]
+    lib.polfed_mlp_set_scaling.argtypes = [c_void_p] + [POINTER(c_float)] * 4
+    lib.polfed_mlp_forward.argtypes = [c_void_p, c_void_p, c_int32, c_void_p, c_void_p]
+    lib.polfed_mlp_grad.argtypes = [c_void_p, c_void_p, c_void_p, c_int32, c_void_p, POINTER(c_float), c_void_p]
+    lib.polfed_mlp_train_step.argtypes = [c_void_p, c_void_p, c_void_p, c_int32, c_float, POINTER(c_float), c_void_p]
+    lib.polfed_mlp_features.argtypes = [POINTER(CModel), c_double, POINTER(c_float)]
+    lib.polfed_mlp_targets.argtypes = [c_int32, POINTER(c_double), POINTER(c_float)]
+    lib.polfed_mlp_predict.argtypes = [c_void_p, POINTER(CModel), c_double, POINTER(c_double)]
+    lib.polfed_cheb_filter_batched.argtypes = [c_int32, POINTER(CModel), POINTER(c_double), POINTER(c_double),
+                                               POINTER(c_double), POINTER(c_int32), POINTER(c_void_p),
+                                               POINTER(c_void_p), c_int32, c_int32, c_int32, c_void_p]
+    lib.polfed_eigs_batched.argtypes = [c_int32, c_int32, POINTER(CModel), POINTER(c_double), POINTER(c_int32),
+                                        POINTER(c_int32), c_int32, POINTER(COpts), c_int32, POINTER(c_double),
+                                        POINTER(c_double), POINTER(c_void_p), POINTER(CStats), POINTER(c_int32),
+                                        POINTER(CBatchInfo)]
     for name in EXPORTED:
         getattr(lib, name)
     _lib = lib
@@ -246,3 +292,168 @@ def eigs(ctx, model, eps_target, N_ev, K=0, n_b=64, opts=None, d_evecs=None, all
                             resid.ctypes.data_as(POINTER(c_double)), byref(st))
     _check(rc, allow=(POLFED_ENOCONV,) if allow_noconv else ())
     return evals, resid, st.as_dict(), rc
+
+
+def _dptr(a):
+    return a.ctypes.data_as(POINTER(c_double))
+
+
+def _fptr(a):
+    return a.ctypes.data_as(POINTER(c_float))
+
+
+def spectral_bounds(ctx, model):
+    """polfed_spectral_bounds: (E_min, E_max, err)."""
+    m = Model.of(model)
+    out = np.zeros(3)
+    _check(load().polfed_spectral_bounds(ctx.h, byref(m.c), _dptr(out)))
+    return float(out[0]), float(out[1]), float(out[2])
+
+
+def kpm_moments(model, d_states, dim, e_lo, e_hi, n_mom, R_block, R, dtype, stream=None):
+    """polfed_kpm_moments: numpy array of n_mom moments."""
+    m = Model.of(model)
+    mu = np.zeros(int(n_mom))
+    _check(load().polfed_kpm_moments(byref(m.c), _ptr(d_states), int(dim), float(e_lo), float(e_hi), int(n_mom),
+                                     _ptr(R_block), int(R), int(dtype), _dptr(mu), _stream(stream)))
+    return mu
+
+
+def kpm_count(mu, x_a, x_b) -> float:
+    mu = np.ascontiguousarray(np.asarray(mu, dtype=np.float64))
+    f = c_double(0.0)
+    _check(load().polfed_kpm_count(_dptr(mu), int(mu.size), float(x_a), float(x_b), byref(f)))
+    return f.value
+
+
+def spectral_labels(ctx, model, eps_target=0.5, n_mom=256, R=16):
+    """polfed_spectral_labels: (E_min, E_max, rho_eps)."""
+    m = Model.of(model)
+    out = np.zeros(3)
+    _check(load().polfed_spectral_labels(ctx.h, byref(m.c), float(eps_target), int(n_mom), int(R), _dptr(out)))
+    return float(out[0]), float(out[1]), float(out[2])
+
+
+def mlp_features(model, W):
+    m = Model.of(model)
+    x = np.zeros(m.c.L + 1, dtype=np.float32)
+    _check(load().polfed_mlp_features(byref(m.c), float(W), _fptr(x)))
+    return x
+
+
+def mlp_targets(L, labels):
+    lab = np.ascontiguousarray(np.asarray(labels, dtype=np.float64))
+    y = np.zeros(3, dtype=np.float32)
+    _check(load().polfed_mlp_targets(int(L), _dptr(lab), _fptr(y)))
+    return y
+
+
+class MLP:
+    """polfed_mlp: the learned spectral predictor (device-resident FP32 network)."""
+
+    def __init__(self, d_in, hidden=128, d_out=3, seed=0):
+        self.lib = load()
+        h = c_void_p()
+        _check(self.lib.polfed_mlp_create(int(d_in), int(hidden), int(d_out), int(seed), byref(h)))
+        self.h = h
+        self.d_in, self.hidden, self.d_out = int(d_in), int(hidden), int(d_out)
+
+    def close(self):
+        if self.h:
+            self.lib.polfed_mlp_destroy(self.h)
+            self.h = c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def num_params(self) -> int:
+        return int(self.lib.polfed_mlp_num_params(self.h))
+
+    def get_params(self):
+        p = np.zeros(self.num_params, dtype=np.float32)
+        _check(self.lib.polfed_mlp_get_params(self.h, _fptr(p)))
+        return p
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(np.asarray(p, dtype=np.float32))
+        assert p.size == self.num_params
+        _check(self.lib.polfed_mlp_set_params(self.h, _fptr(p)))
+
+    def set_scaling(self, x_mean, x_std, y_mean, y_std):
+        a = [np.ascontiguousarray(np.asarray(v, dtype=np.float32)) for v in (x_mean, x_std, y_mean, y_std)]
+        _check(self.lib.polfed_mlp_set_scaling(self.h, *[_fptr(v) for v in a]))
+
+    def forward(self, d_x, B, d_y, stream=None):
+        _check(self.lib.polfed_mlp_forward(self.h, _ptr(d_x), int(B), _ptr(d_y), _stream(stream)))
+
+    def grad(self, d_x, d_t, B, d_grad=None, stream=None) -> float:
+        loss = c_float(0.0)
+        _check(self.lib.polfed_mlp_grad(self.h, _ptr(d_x), _ptr(d_t), int(B), _ptr(d_grad), byref(loss),
+                                        _stream(stream)))
+        return loss.value
+
+    def train_step(self, d_x, d_t, B, lr, stream=None) -> float:
+        loss = c_float(0.0)
+        _check(self.lib.polfed_mlp_train_step(self.h, _ptr(d_x), _ptr(d_t), int(B), float(lr), byref(loss),
+                                              _stream(stream)))
+        return loss.value
+
+    def predict(self, model, W):
+        """(E_min, E_max, rho_eps) for one realization."""
+        m = Model.of(model)
+        out = np.zeros(3)
+        _check(self.lib.polfed_mlp_predict(self.h, byref(m.c), float(W), _dptr(out)))
+        return float(out[0]), float(out[1]), float(out[2])
+
+
+def _models_array(models):
+    ms = [Model.of(m) for m in models]
+    arr = (CModel * len(ms))(*[m.c for m in ms])
+    return ms, arr
+
+
+def cheb_filter_batched(models, e_lo, e_hi, sigma, K, Xs, Ys, n_b, dtype, ctas_per_sm=0, stream=None):
+    """polfed_cheb_filter_batched: all realizations' filters in one cooperative launch."""
+    n = len(models)
+    keep, arr = _models_array(models)
+    lo = np.ascontiguousarray(e_lo, dtype=np.float64)
+    hi = np.ascontiguousarray(e_hi, dtype=np.float64)
+    sg = np.ascontiguousarray(sigma, dtype=np.float64)
+    kk = np.ascontiguousarray(K, dtype=np.int32)
+    xp = (c_void_p * n)(*[_ptr(x) for x in Xs])
+    yp = (c_void_p * n)(*[_ptr(y) for y in Ys])
+    return _check(load().polfed_cheb_filter_batched(n, arr, _dptr(lo), _dptr(hi), _dptr(sg),
+                                                    kk.ctypes.data_as(POINTER(c_int32)), xp, yp, int(n_b),
+                                                    int(dtype), int(ctas_per_sm), _stream(stream)))
+
+
+def eigs_batched(models, eps_target, N_ev, K=None, n_b=0, opts=None, max_workers=0, d_evecs=None, device=0,
+                 allow_fail=False):
+    """polfed_eigs_batched: returns (list of evals, list of resid, list of stats dicts, statuses, info dict, rc)."""
+    n = len(models)
+    keep, arr = _models_array(models)
+    eps = np.ascontiguousarray(np.broadcast_to(np.asarray(eps_target, dtype=np.float64), (n,)))
+    nev = np.ascontiguousarray(np.broadcast_to(np.asarray(N_ev, dtype=np.int32), (n,)))
+    kk = None if K is None else np.ascontiguousarray(np.broadcast_to(np.asarray(K, dtype=np.int32), (n,)))
+    tot = int(nev.sum())
+    ev = np.zeros(tot)
+    rs = np.zeros(tot)
+    st = (CStats * n)()
+    status = np.zeros(n, dtype=np.int32)
+    info = CBatchInfo()
+    o = opts if opts is not None else opts_default()
+    vp = None if d_evecs is None else (c_void_p * n)(*[_ptr(v) for v in d_evecs])
+    rc = load().polfed_eigs_batched(int(device), n, arr, _dptr(eps), nev.ctypes.data_as(POINTER(c_int32)),
+                                    None if kk is None else kk.ctypes.data_as(POINTER(c_int32)), int(n_b), byref(o),
+                                    int(max_workers), _dptr(ev), _dptr(rs), vp, st,
+                                    status.ctypes.data_as(POINTER(c_int32)), byref(info))
+    if not allow_fail:
+        _check(rc)
+    offs = np.concatenate([[0], np.cumsum(nev)])
+    evs = [ev[offs[i]:offs[i + 1]] for i in range(n)]
+    res = [rs[offs[i]:offs[i + 1]] for i in range(n)]
+    return evs, res, [s.as_dict() for s in st], status, info.as_dict(), rc

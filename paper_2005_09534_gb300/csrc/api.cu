@@ -9,7 +9,7 @@
 namespace polfed {
 
 static thread_local std::string t_err;
-static Counters g_counters;
+static thread_local Counters g_counters;  // per host thread: a call reports its own launches
 Counters& counters() { return g_counters; }
 
 void set_error(int code, const std::string& msg) { t_err = "[" + std::to_string(code) + "] " + msg; }
@@ -69,8 +69,13 @@ void polfed_opts_default(polfed_opts* o) {
   o->precision = POLFED_DF64;
   o->bounds_steps = 600;
   o->verbose = 0;
-  o->reserved = 0;
+  o->dos_rule = POLFED_DOS_MOMENTS;
   o->seed = 1234;
+  o->rho_hint = 0.0;
+  o->emin_hint = 0.0;
+  o->emax_hint = 0.0;
+  o->kpm_moments = 256;
+  o->kpm_vectors = 16;
 }
 
 int polfed_basis_build(int32_t L, int32_t n_up, uint32_t* d_states, int64_t* dim, polfed_stream_t stream) {

@@ -406,6 +406,225 @@ struct StepTables {
   const int32_t* order;
 };
 
+template <bool COH>
+__device__ __forceinline__ int4 ld_vec(const int4* p) {
+  if constexpr (COH)
+    return __ldcg(p);  // L2 only: data written earlier in the same (persistent) launch
+  else
+    return __ldg(p);
+}
+template <bool COH>
+__device__ __forceinline__ int4 ld_stream(const int4* p) {
+  if constexpr (COH)
+    return __ldcg(p);
+  else
+    return __ldcs(p);
+}
+
+// One group (rows sharing s_hi) of one Clenshaw / H~ step on a 16*LPR-byte
+// column slice, by the CTA's 256 threads (see k_ham_step).  COH selects loads
+// that bypass L1, for a persistent kernel whose earlier steps wrote b1 and b2.
+template <class NT, int LPR, bool J2, bool COH>
+__device__ __forceinline__ void step_group(const int gidx, const int n_cross, const int* cr_lb, const int* cr_c2,
+                                           const StepTables& t, const typename NT::S* __restrict__ b1,
+                                           const typename NT::S* b2, const typename NT::S* __restrict__ x,
+                                           typename NT::S* out, const typename NT::KC& kc, const int has_x,
+                                           const int has_b2, typename NT::S* tile, const typename NT::C* sFlo,
+                                           const typename NT::C* sCx) {
+  using S = typename NT::S;
+  using C = typename NT::C;
+  using A = typename NT::A;
+  constexpr int VEC = 16 / sizeof(S);
+  constexpr int W = VEC * LPR;
+  constexpr int MAXCR = J2 ? 6 : 2;  // cross bonds: (b-1,b), (L-1,0) and, with J2, four more
+  constexpr int RS = J2 ? 32 : 16;   // record entries
+  constexpr int LOWMAX = RS - 2 - MAXCR;
+  constexpr int PCH = J2 ? 2 : 4;    // rows per thread per pass
+  constexpr int NT_ = 256;
+  constexpr int RSTEP = NT_ / LPR;   // rows between a thread's consecutive rows in a pass
+  const int tr = threadIdx.x / LPR, lane = threadIdx.x % LPR;
+  const typename NT::C* gFhi = reinterpret_cast<const typename NT::C*>(t.F_hi);
+  const GroupRec* G = t.grec + gidx;
+  const int r0 = __ldg(&G->r0), n_g = __ldg(&G->n_g), cls_base = __ldg(&G->cls_base);
+  const int n_hn = __ldg(&G->n_hn), n_hn1 = __ldg(&G->n_hn1), need = __ldg(&G->need_mask);
+  int cr_bs[MAXCR];
+#pragma unroll
+  for (int k = 0; k < MAXCR; k++) cr_bs[k] = __ldg(&G->cr_base[k]);
+  const C fhi = gFhi[t.order[gidx]];
+  __syncthreads();  // tables loaded / previous tile fully consumed
+  {
+    const int4* src = reinterpret_cast<const int4*>(b1 + (size_t)r0 * W);
+    int4* dst = reinterpret_cast<int4*>(tile);
+    const int nchunk = n_g * LPR;
+    for (int c = threadIdx.x; c < nchunk; c += NT_) dst[c] = ld_vec<COH>(src + c);
+  }
+  __syncthreads();
+  for (int p0 = 0; p0 < n_g; p0 += RSTEP * PCH) {
+    A a1[PCH][VEC], a2[PCH][VEC];
+#pragma unroll
+    for (int i = 0; i < PCH; i++)
+#pragma unroll
+      for (int v = 0; v < VEC; v++) {
+        a1[i][v] = NT::zero();
+        a2[i][v] = NT::zero();
+      }
+    // ---- H: high-bond neighbours: the same local rows of another group;
+    //      loads of HU neighbours x PCH rows are issued before any is consumed
+    constexpr int HU = 2;
+    for (int k0 = 0; k0 < n_hn; k0 += HU) {
+      V16<S> u[HU][PCH];
+#pragma unroll
+      for (int j = 0; j < HU; j++) {
+        if (k0 + j < n_hn) {
+          const int base = __ldg(&G->hn_base[k0 + j]);
+#pragma unroll
+          for (int i = 0; i < PCH; i++) {
+            const int row = p0 + tr + RSTEP * i;
+            if (row < n_g)
+              u[j][i].i = ld_vec<COH>(reinterpret_cast<const int4*>(b1 + (size_t)(base + row) * W + lane * VEC));
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < HU; j++) {
+        if (k0 + j < n_hn) {
+          const bool c1 = !J2 || k0 + j < n_hn1;
+#pragma unroll
+          for (int i = 0; i < PCH; i++) {
+            const int row = p0 + tr + RSTEP * i;
+            if (row < n_g) {
+              if (c1) {
+#pragma unroll
+                for (int v = 0; v < VEC; v++) NT::acc(a1[i][v], u[j][i].s[v]);
+              } else {
+#pragma unroll
+                for (int v = 0; v < VEC; v++) NT::acc(a2[i][v], u[j][i].s[v]);
+              }
+            }
+          }
+        }
+      }
+    }
+    // ---- L + C: low bonds (shared memory) and cross bonds (global), LR rows at a time:
+    //      records of all LR rows first, then their cross-bond loads, then the gathers
+    constexpr int LR = J2 ? 1 : 2;
+    uint32_t key[PCH];  // s_lo | cross pattern << 16
+#pragma unroll
+    for (int i0 = 0; i0 < PCH; i0 += LR) {
+      uint32_t rw[LR][RS / 2];
+#pragma unroll
+      for (int j = 0; j < LR; j++) {
+        const int row = p0 + tr + RSTEP * (i0 + j);
+        const uint4* rp = reinterpret_cast<const uint4*>(t.rec + (size_t)(cls_base + (row < n_g ? row : 0)) * RS);
+#pragma unroll
+        for (int q = 0; q < RS / 8; q++) {
+          const uint4 v = __ldg(rp + q);
+          rw[j][4 * q] = v.x;
+          rw[j][4 * q + 1] = v.y;
+          rw[j][4 * q + 2] = v.z;
+          rw[j][4 * q + 3] = v.w;
+        }
+      }
+#define PF_ENTRY(j, e) ((rw[j][(e) >> 1] >> (((e)&1) * 16)) & 0xFFFFu)
+      V16<S> cv[LR][MAXCR];
+      uint32_t pat[LR];
+#pragma unroll
+      for (int j = 0; j < LR; j++) {
+        const int row = p0 + tr + RSTEP * (i0 + j);
+        const uint32_t s_lo = PF_ENTRY(j, 0);
+        pat[j] = 0;
+#pragma unroll
+        for (int k = 0; k < MAXCR; k++) {
+          if (row < n_g && k < n_cross && ((s_lo >> cr_lb[k]) & 1u) == ((need >> k) & 1)) {
+            pat[j] |= 1u << k;
+            cv[j][k].i = ld_vec<COH>(
+                reinterpret_cast<const int4*>(b1 + (size_t)(cr_bs[k] + PF_ENTRY(j, RS - 1 - k)) * W + lane * VEC));
+          }
+        }
+        key[i0 + j] = s_lo | (pat[j] << 16);
+      }
+#pragma unroll
+      for (int j = 0; j < LR; j++) {
+        const int i = i0 + j;
+        const int row = p0 + tr + RSTEP * i;
+        const uint32_t cnt = PF_ENTRY(j, 1);
+        const int n1 = row < n_g ? (int)(cnt & 0xFF) : 0;
+        const int nl = row < n_g ? n1 + (J2 ? (int)(cnt >> 8) : 0) : 0;
+        const int nmax = __reduce_max_sync(0xffffffffu, nl);
+#pragma unroll
+        for (int k0 = 0; k0 < LOWMAX; k0 += 4) {
+          if (k0 >= nmax) break;
+          V16<S> u[4];
+#pragma unroll
+          for (int q = 0; q < 4; q++) {
+            const int k = k0 + q;
+            if (k < LOWMAX && k < nl)
+              u[q].i = *reinterpret_cast<const int4*>(tile + (size_t)PF_ENTRY(j, 2 + k) * W + lane * VEC);
+          }
+#pragma unroll
+          for (int q = 0; q < 4; q++) {
+            const int k = k0 + q;
+            if (k < LOWMAX && k < nl) {
+              if (!J2 || k < n1) {
+#pragma unroll
+                for (int v = 0; v < VEC; v++) NT::acc(a1[i][v], u[q].s[v]);
+              } else {
+#pragma unroll
+                for (int v = 0; v < VEC; v++) NT::acc(a2[i][v], u[q].s[v]);
+              }
+            }
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < MAXCR; k++) {
+          if ((pat[j] >> k) & 1u) {
+            if (!J2 || !cr_c2[k]) {
+#pragma unroll
+              for (int v = 0; v < VEC; v++) NT::acc(a1[i][v], cv[j][k].s[v]);
+            } else {
+#pragma unroll
+              for (int v = 0; v < VEC; v++) NT::acc(a2[i][v], cv[j][k].s[v]);
+            }
+          }
+        }
+      }
+#undef PF_ENTRY
+    }
+    // ---- F: diagonal, combination, store (x and b2 loads issued per chunk of rows)
+    constexpr int FCH = 2;
+#pragma unroll
+    for (int i0 = 0; i0 < PCH; i0 += FCH) {
+      V16<S> xv[FCH], bv[FCH];
+#pragma unroll
+      for (int j = 0; j < FCH; j++) {
+        const int row = p0 + tr + RSTEP * (i0 + j);
+        if (row < n_g) {
+          const size_t off = (size_t)(r0 + row) * W + lane * VEC;
+          if (has_x) xv[j].i = ld_stream<COH>(reinterpret_cast<const int4*>(x + off));
+          if (has_b2) bv[j].i = ld_stream<COH>(reinterpret_cast<const int4*>(b2 + off));
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < FCH; j++) {
+        const int i = i0 + j;
+        const int row = p0 + tr + RSTEP * i;
+        if (row < n_g) {
+          const size_t off = (size_t)(r0 + row) * W + lane * VEC;
+          const uint32_t s_lo = key[i] & 0xFFFFu, pattern = key[i] >> 16;
+          const C ad = NT::add3(sFlo[s_lo], fhi, sCx[pattern]);
+          V16<S> xo, res;
+          xo.i = *reinterpret_cast<const int4*>(tile + (size_t)row * W + lane * VEC);
+#pragma unroll
+          for (int v = 0; v < VEC; v++)
+            res.s[v] = NT::combine(has_x ? xv[j].s[v] : S(), xo.s[v], has_b2 ? bv[j].s[v] : S(), a1[i][v],
+                                   a2[i][v], ad, kc, has_x, has_b2, J2);
+          __stcg(reinterpret_cast<int4*>(out + off), res.i);
+        }
+      }
+    }
+  }
+}
+
 // One Clenshaw / H~ step on a 16*LPR-byte column slice:
 //   out = cX * x + cH * (H~ b1) + cB * b2     (row-major slice buffers, ld = W)
 // A CTA takes groups in schedule order; a group's rows of b1 are staged in
@@ -439,12 +658,10 @@ __global__ void __launch_bounds__(256, 2) k_ham_step(const HamGeometry g, const 
   C* sCx = sFlo + nlo_tab;
 
   const C* gFlo = reinterpret_cast<const C*>(t.F_lo);
-  const C* gFhi = reinterpret_cast<const C*>(t.F_hi);
   const C* gCx = reinterpret_cast<const C*>(t.C_x);
   for (int i = threadIdx.x; i < nlo_tab; i += NT_) sFlo[i] = gFlo[i];
   for (int i = threadIdx.x; i < (1 << g.n_cross); i += NT_) sCx[i] = gCx[i];
 
-  const int tr = threadIdx.x / LPR, lane = threadIdx.x % LPR;
   int cr_lb[MAXCR], cr_c2[MAXCR];
 #pragma unroll
   for (int k = 0; k < MAXCR; k++) {
@@ -452,186 +669,149 @@ __global__ void __launch_bounds__(256, 2) k_ham_step(const HamGeometry g, const 
     cr_c2[k] = k < g.n_cross && g.cross_cls[k] == 2;
   }
 
-  for (int gidx = blockIdx.x; gidx < g.n_groups; gidx += gridDim.x) {
-    const GroupRec* G = t.grec + gidx;
-    const int r0 = __ldg(&G->r0), n_g = __ldg(&G->n_g), cls_base = __ldg(&G->cls_base);
-    const int n_hn = __ldg(&G->n_hn), n_hn1 = __ldg(&G->n_hn1), need = __ldg(&G->need_mask);
-    int cr_bs[MAXCR];
-#pragma unroll
-    for (int k = 0; k < MAXCR; k++) cr_bs[k] = __ldg(&G->cr_base[k]);
-    const C fhi = gFhi[t.order[gidx]];
-    __syncthreads();  // tables loaded / previous tile fully consumed
-    {
-      const int4* src = reinterpret_cast<const int4*>(b1 + (size_t)r0 * W);
-      int4* dst = reinterpret_cast<int4*>(tile);
-      const int nchunk = n_g * LPR;
-      for (int c = threadIdx.x; c < nchunk; c += NT_) dst[c] = __ldg(src + c);
-    }
-    __syncthreads();
-    for (int p0 = 0; p0 < n_g; p0 += RSTEP * PCH) {
-      A a1[PCH][VEC], a2[PCH][VEC];
-#pragma unroll
-      for (int i = 0; i < PCH; i++)
-#pragma unroll
-        for (int v = 0; v < VEC; v++) {
-          a1[i][v] = NT::zero();
-          a2[i][v] = NT::zero();
+  for (int gidx = blockIdx.x; gidx < g.n_groups; gidx += gridDim.x)
+    step_group<NT, LPR, J2, false>(gidx, g.n_cross, cr_lb, cr_c2, t, b1, b2, x, out, kc, has_x, has_b2, tile, sFlo,
+                                   sCx);
+}
+
+// ------------------------------------------------ batched persistent filter
+// Many independent filter jobs -- one 128-byte column slice of one disorder
+// realization each, with its own operator tables, order K and coefficients --
+// advance through their Clenshaw steps inside ONE cooperative launch.  Launch
+// step st performs step st of every job with st < K_j (Clenshaw index
+// k = K_j - 1 - st): the CTAs share out the groups of all active jobs in a
+// fixed order, then meet at a grid barrier.  The barrier's waits are bounded;
+// a wait that runs out sets *err and every CTA leaves at its next barrier.
+struct BatchJob {
+  StepTables t;
+  const double* coef;  // c_0..c_K of the job (device, FP64)
+  void* xs;            // slice buffers (dim x W, storage type of the kernel)
+  void* ba;
+  void* bb;
+  double invD, o1, o2;
+  int K, n_groups, n_cross, nlo_tab;
+  int cross_lo[6], cross_cls[6];
+};
+
+__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, int* err) {
+  __syncthreads();
+  int ok = 1;
+  if (threadIdx.x == 0) {
+    const unsigned g0 = *(volatile unsigned*)gen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(count, 1u) + 1u;
+    if (arrived == gridDim.x) {
+      atomicExch(count, 0u);
+      __threadfence();
+      atomicAdd(gen, 1u);
+    } else {
+      uint32_t it = 0;
+      while (*(volatile unsigned*)gen == g0) {
+        if (*(volatile int*)err) {
+          ok = 0;
+          break;
         }
-      // ---- H: high-bond neighbours: the same local rows of another group;
-      //      loads of HU neighbours x PCH rows are issued before any is consumed
-      constexpr int HU = 2;
-      for (int k0 = 0; k0 < n_hn; k0 += HU) {
-        V16<S> u[HU][PCH];
-#pragma unroll
-        for (int j = 0; j < HU; j++) {
-          if (k0 + j < n_hn) {
-            const int base = __ldg(&G->hn_base[k0 + j]);
-#pragma unroll
-            for (int i = 0; i < PCH; i++) {
-              const int row = p0 + tr + RSTEP * i;
-              if (row < n_g)
-                u[j][i].i = __ldg(reinterpret_cast<const int4*>(b1 + (size_t)(base + row) * W + lane * VEC));
-            }
-          }
+        if (++it > (1u << 24)) {  // about a second of 32-64 ns naps
+          atomicExch(err, 1);
+          ok = 0;
+          break;
         }
-#pragma unroll
-        for (int j = 0; j < HU; j++) {
-          if (k0 + j < n_hn) {
-            const bool c1 = !J2 || k0 + j < n_hn1;
-#pragma unroll
-            for (int i = 0; i < PCH; i++) {
-              const int row = p0 + tr + RSTEP * i;
-              if (row < n_g) {
-                if (c1) {
-#pragma unroll
-                  for (int v = 0; v < VEC; v++) NT::acc(a1[i][v], u[j][i].s[v]);
-                } else {
-#pragma unroll
-                  for (int v = 0; v < VEC; v++) NT::acc(a2[i][v], u[j][i].s[v]);
-                }
-              }
-            }
-          }
-        }
-      }
-      // ---- L + C: low bonds (shared memory) and cross bonds (global), LR rows at a time:
-      //      records of all LR rows first, then their cross-bond loads, then the gathers
-      constexpr int LR = J2 ? 1 : 2;
-      uint32_t key[PCH];  // s_lo | cross pattern << 16
-#pragma unroll
-      for (int i0 = 0; i0 < PCH; i0 += LR) {
-        uint32_t rw[LR][RS / 2];
-#pragma unroll
-        for (int j = 0; j < LR; j++) {
-          const int row = p0 + tr + RSTEP * (i0 + j);
-          const uint4* rp = reinterpret_cast<const uint4*>(t.rec + (size_t)(cls_base + (row < n_g ? row : 0)) * RS);
-#pragma unroll
-          for (int q = 0; q < RS / 8; q++) {
-            const uint4 v = __ldg(rp + q);
-            rw[j][4 * q] = v.x;
-            rw[j][4 * q + 1] = v.y;
-            rw[j][4 * q + 2] = v.z;
-            rw[j][4 * q + 3] = v.w;
-          }
-        }
-#define PF_ENTRY(j, e) ((rw[j][(e) >> 1] >> (((e)&1) * 16)) & 0xFFFFu)
-        V16<S> cv[LR][MAXCR];
-        uint32_t pat[LR];
-#pragma unroll
-        for (int j = 0; j < LR; j++) {
-          const int row = p0 + tr + RSTEP * (i0 + j);
-          const uint32_t s_lo = PF_ENTRY(j, 0);
-          pat[j] = 0;
-#pragma unroll
-          for (int k = 0; k < MAXCR; k++) {
-            if (row < n_g && k < g.n_cross && ((s_lo >> cr_lb[k]) & 1u) == ((need >> k) & 1)) {
-              pat[j] |= 1u << k;
-              cv[j][k].i = __ldg(
-                  reinterpret_cast<const int4*>(b1 + (size_t)(cr_bs[k] + PF_ENTRY(j, RS - 1 - k)) * W + lane * VEC));
-            }
-          }
-          key[i0 + j] = s_lo | (pat[j] << 16);
-        }
-#pragma unroll
-        for (int j = 0; j < LR; j++) {
-          const int i = i0 + j;
-          const int row = p0 + tr + RSTEP * i;
-          const uint32_t cnt = PF_ENTRY(j, 1);
-          const int n1 = row < n_g ? (int)(cnt & 0xFF) : 0;
-          const int nl = row < n_g ? n1 + (J2 ? (int)(cnt >> 8) : 0) : 0;
-          const int nmax = __reduce_max_sync(0xffffffffu, nl);
-#pragma unroll
-          for (int k0 = 0; k0 < LOWMAX; k0 += 4) {
-            if (k0 >= nmax) break;
-            V16<S> u[4];
-#pragma unroll
-            for (int q = 0; q < 4; q++) {
-              const int k = k0 + q;
-              if (k < LOWMAX && k < nl)
-                u[q].i = *reinterpret_cast<const int4*>(tile + (size_t)PF_ENTRY(j, 2 + k) * W + lane * VEC);
-            }
-#pragma unroll
-            for (int q = 0; q < 4; q++) {
-              const int k = k0 + q;
-              if (k < LOWMAX && k < nl) {
-                if (!J2 || k < n1) {
-#pragma unroll
-                  for (int v = 0; v < VEC; v++) NT::acc(a1[i][v], u[q].s[v]);
-                } else {
-#pragma unroll
-                  for (int v = 0; v < VEC; v++) NT::acc(a2[i][v], u[q].s[v]);
-                }
-              }
-            }
-          }
-#pragma unroll
-          for (int k = 0; k < MAXCR; k++) {
-            if ((pat[j] >> k) & 1u) {
-              if (!J2 || !cr_c2[k]) {
-#pragma unroll
-                for (int v = 0; v < VEC; v++) NT::acc(a1[i][v], cv[j][k].s[v]);
-              } else {
-#pragma unroll
-                for (int v = 0; v < VEC; v++) NT::acc(a2[i][v], cv[j][k].s[v]);
-              }
-            }
-          }
-        }
-#undef PF_ENTRY
-      }
-      // ---- F: diagonal, combination, store (x and b2 loads issued per chunk of rows)
-      constexpr int FCH = 2;
-#pragma unroll
-      for (int i0 = 0; i0 < PCH; i0 += FCH) {
-        V16<S> xv[FCH], bv[FCH];
-#pragma unroll
-        for (int j = 0; j < FCH; j++) {
-          const int row = p0 + tr + RSTEP * (i0 + j);
-          if (row < n_g) {
-            const size_t off = (size_t)(r0 + row) * W + lane * VEC;
-            if (has_x) xv[j].i = __ldcs(reinterpret_cast<const int4*>(x + off));
-            if (has_b2) bv[j].i = __ldcs(reinterpret_cast<const int4*>(b2 + off));
-          }
-        }
-#pragma unroll
-        for (int j = 0; j < FCH; j++) {
-          const int i = i0 + j;
-          const int row = p0 + tr + RSTEP * i;
-          if (row < n_g) {
-            const size_t off = (size_t)(r0 + row) * W + lane * VEC;
-            const uint32_t s_lo = key[i] & 0xFFFFu, pattern = key[i] >> 16;
-            const C ad = NT::add3(sFlo[s_lo], fhi, sCx[pattern]);
-            V16<S> xo, res;
-            xo.i = *reinterpret_cast<const int4*>(tile + (size_t)row * W + lane * VEC);
-#pragma unroll
-            for (int v = 0; v < VEC; v++)
-              res.s[v] = NT::combine(has_x ? xv[j].s[v] : S(), xo.s[v], has_b2 ? bv[j].s[v] : S(), a1[i][v],
-                                     a2[i][v], ad, kc, has_x, has_b2, J2);
-            __stcg(reinterpret_cast<int4*>(out + off), res.i);
-          }
-        }
+        __nanosleep(32);
       }
     }
+    __threadfence();
+  }
+  return __syncthreads_and(ok) != 0;
+}
+
+template <class NT>
+__device__ __forceinline__ void make_kc(double cX, double cH, double cB, double o1, double o2, typename NT::KC& kc) {
+  if constexpr (std::is_same<NT, NDF>::value) {
+    auto split = [](double v) {
+      const float hi = (float)v;
+      return make_float2(hi, (float)(v - (double)hi));
+    };
+    auto p2 = [](double v) {
+      if (v == 0.0) return true;
+      int e = 0;
+      const double m = frexp(fabs(v), &e);
+      return m == 0.5 && e > -120 && e < 120;
+    };
+    kc.cX = split(cX);
+    kc.cH = split(cH);
+    kc.cB = split(cB);
+    kc.o1 = split(o1);
+    kc.o2 = split(o2);
+    kc.exact = p2(cX) && p2(cH) && p2(cB);
+  } else {
+    using C = typename NT::C;
+    kc.cX = (C)cX;
+    kc.cH = (C)cH;
+    kc.cB = (C)cB;
+    kc.o1 = (C)o1;
+    kc.o2 = (C)o2;
+  }
+}
+
+template <class NT, bool J2>
+__global__ void __launch_bounds__(256, 2)
+    k_filter_batched(const BatchJob* __restrict__ jobs, int n_jobs, int n_steps, int tile_elems, int nlo_max,
+                     unsigned* bar_count, unsigned* bar_gen, int* err) {
+  using S = typename NT::S;
+  using C = typename NT::C;
+  constexpr int LPR = 8;
+  constexpr int MAXCR = J2 ? 6 : 2;
+  extern __shared__ __align__(16) unsigned char smem[];
+  S* tile = reinterpret_cast<S*>(smem);
+  C* sFlo = reinterpret_cast<C*>(smem + (size_t)tile_elems * sizeof(S));
+  C* sCx = sFlo + nlo_max;
+  int loaded = -1, n_cross = 0;
+  int cr_lb[MAXCR], cr_c2[MAXCR];
+  const int G = gridDim.x;
+  for (int st = 0; st < n_steps; st++) {
+    int base = 0;
+    for (int j = 0; j < n_jobs; j++) {
+      const int K = jobs[j].K;
+      if (st >= K) continue;
+      const int ng = jobs[j].n_groups;
+      for (int w = base + (int)((blockIdx.x + G - (unsigned)base % G) % G); w < base + ng; w += G) {
+        const BatchJob& J = jobs[j];
+        if (loaded != j) {
+          __syncthreads();  // the previous job's tables and tile are no longer read
+          const C* gFlo = reinterpret_cast<const C*>(J.t.F_lo);
+          const C* gCx = reinterpret_cast<const C*>(J.t.C_x);
+          for (int i = threadIdx.x; i < J.nlo_tab; i += 256) sFlo[i] = gFlo[i];
+          for (int i = threadIdx.x; i < (1 << J.n_cross); i += 256) sCx[i] = gCx[i];
+          n_cross = J.n_cross;
+#pragma unroll
+          for (int k = 0; k < MAXCR; k++) {
+            cr_lb[k] = k < n_cross ? J.cross_lo[k] : 0;
+            cr_c2[k] = k < n_cross && J.cross_cls[k] == 2;
+          }
+          loaded = j;
+        }
+        const int kk = K - 1 - st;
+        S* cur = reinterpret_cast<S*>((st & 1) ? J.bb : J.ba);  // b_{k+1}
+        S* oth = reinterpret_cast<S*>((st & 1) ? J.ba : J.bb);  // b_{k+2}, overwritten by b_k
+        typename NT::KC kc;
+        double cX, cH, cB;
+        if (kk >= 1) {
+          cX = J.coef[kk];
+          cH = 2.0;
+          cB = (kk == K - 1) ? 0.0 : -1.0;
+        } else {  // Y = (c_0 X + H~ b_1 - b_2) / D
+          cX = J.coef[0] * J.invD;
+          cH = J.invD;
+          cB = (K == 1) ? 0.0 : -J.invD;
+        }
+        make_kc<NT>(cX, cH, cB, J.o1, J.o2, kc);
+        step_group<NT, LPR, J2, true>(w - base, n_cross, cr_lb, cr_c2, J.t, cur, oth,
+                                      reinterpret_cast<const S*>(J.xs), oth, kc, cX != 0.0, cB != 0.0, tile, sFlo,
+                                      sCx);
+      }
+      base += ng;
+    }
+    if (!grid_barrier(bar_count, bar_gen, err)) return;
   }
 }
 
@@ -1611,6 +1791,219 @@ int apply_block(HamPlan& plan, int kind, const void* in, void* out, int n_b, int
     PF_CHECK(slice_out(kind, abi_kind, scr.ba, dim, W, ncols, out, n_b, col0, scr.flag, s));
   }
   PF_CHECK(check_timeout(plan, s));
+  return POLFED_OK;
+}
+
+// ------------------------------------------------ batched filter (host side)
+namespace {
+
+struct BatchLayout {
+  size_t jobs_off, coef_off, flags_off, bar_off, slices_off, total;
+  int n_jobs;
+};
+
+int batch_width(int kind) { return slice_width(kind, 8); }
+
+BatchLayout batch_layout(const std::vector<BatchFilterItem>& items, int kind) {
+  BatchLayout L{};
+  const int W = batch_width(kind);
+  auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  int n_jobs = 0;
+  size_t coefs = 0, slices = 0;
+  for (const auto& it : items) {
+    const int ns = (it.n_b + W - 1) / W;
+    n_jobs += ns;
+    coefs += (size_t)it.K + 1;
+    const size_t sb = al((size_t)it.plan->geo.dim * W * elem_bytes(kind));
+    slices += (size_t)ns * 3 * sb;
+  }
+  L.n_jobs = n_jobs;
+  L.jobs_off = 0;
+  L.coef_off = al(sizeof(BatchJob) * std::max(1, n_jobs));
+  L.flags_off = L.coef_off + al(sizeof(double) * std::max<size_t>(1, coefs));
+  L.bar_off = L.flags_off + al(16 * std::max<size_t>(1, items.size()));
+  L.slices_off = L.bar_off + 256;
+  L.total = L.slices_off + slices;
+  return L;
+}
+
+template <class NT, bool J2>
+int launch_batched(const BatchJob* d_jobs, int n_jobs, int n_steps, int tile_elems, int nlo_max, unsigned* bar,
+                   int* err, int ctas_per_sm, cudaStream_t s, int* grid_out) {
+  using S = typename NT::S;
+  using C = typename NT::C;
+  auto kern = k_filter_batched<NT, J2>;
+  const size_t smem = (size_t)tile_elems * sizeof(S) + ((size_t)nlo_max + 64) * sizeof(C);
+  int dev = 0;
+  PF_CUDA(cudaGetDevice(&dev));
+  int optin = 0, nsm = 0, coop = 0;
+  PF_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  PF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  PF_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  if (!coop) return fail(POLFED_ECUDA, "device does not support cooperative launches");
+  cudaFuncAttributes fa;
+  PF_CUDA(cudaFuncGetAttributes(&fa, kern));
+  if (smem + fa.sharedSizeBytes > (size_t)optin) return fail(POLFED_EINVAL, "batched filter tile does not fit");
+  PF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int occ = 0;
+  PF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, smem));
+  if (occ < 1) return fail(POLFED_EINVAL, "batched filter kernel cannot be resident");
+  const int per_sm = ctas_per_sm > 0 ? std::min(ctas_per_sm, occ) : occ;
+  int grid = nsm * per_sm;  // every CTA co-resident: the grid barrier cannot deadlock
+  unsigned* count = bar;
+  unsigned* gen = bar + 1;
+  void* args[] = {(void*)&d_jobs, (void*)&n_jobs, (void*)&n_steps, (void*)&tile_elems, (void*)&nlo_max,
+                  (void*)&count, (void*)&gen, (void*)&err};
+  PF_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(256), args, smem, s));
+  count_launch();
+  *grid_out = grid;
+  return POLFED_OK;
+}
+
+}  // namespace
+
+size_t batch_scratch_bytes(const std::vector<BatchFilterItem>& items, int kind) {
+  return batch_layout(items, kind).total;
+}
+
+int filter_batched(std::vector<BatchFilterItem>& items, int kind, int abi_kind, void* scratch, size_t bytes,
+                   cudaStream_t s, int ctas_per_sm, BatchStats* bst) {
+  if (items.empty()) return POLFED_OK;
+  if (kind != POLFED_F32 && kind != POLFED_DF64) return fail(POLFED_EINVAL, "batched filter: FP32 or DF64 only");
+  const BatchLayout Lo = batch_layout(items, kind);
+  if (!scratch || bytes < Lo.total) return fail(POLFED_ENOMEM, "batched filter scratch too small");
+  const int W = batch_width(kind);
+  const size_t es = elem_bytes(kind);
+  char* base = (char*)scratch;
+  const bool j2 = items[0].plan->geo.J2 != 0.0;
+  std::vector<BatchJob> jobs;
+  std::vector<double> coefs;
+  jobs.reserve(Lo.n_jobs);
+  size_t slice_pos = Lo.slices_off;
+  int n_steps = 0, tile_elems = 0, nlo_max = 1;
+  double alg = 0.0;
+  const int kk = kind;
+  PF_CUDA(cudaMemsetAsync(base + Lo.flags_off, 0, 16 * items.size(), s));
+  PF_CUDA(cudaMemsetAsync(base + Lo.bar_off, 0, 256, s));
+  for (size_t q = 0; q < items.size(); q++) {
+    BatchFilterItem& it = items[q];
+    HamPlan& p = *it.plan;
+    const HamGeometry& g = p.geo;
+    if ((g.J2 != 0.0) != j2) return fail(POLFED_EINVAL, "batched filter: all jobs must agree on J2 = 0 or not");
+    if (g.n_cross > (j2 ? 6 : 2)) return fail(POLFED_EINVAL, "more cross bonds than the kernel handles");
+    if (g.rec_stride != (j2 ? 32 : 16)) return fail(POLFED_EINVAL, "record layout does not match the kernel");
+    if (!p.typed_ok[kk]) return fail(POLFED_EINVAL, "batched filter: typed tables not prepared");
+    float* flag = (float*)(base + Lo.flags_off + 16 * q);
+    const size_t sb = ((size_t)g.dim * W * es + 255) & ~(size_t)255;
+    const double alpha = (p.typed_lo[kk] == 0.0 && p.typed_hi[kk] == 0.0) ? 1.0 : 2.0 / (p.typed_hi[kk] - p.typed_lo[kk]);
+    const size_t cs = (kk == POLFED_F32 ? 4 : 8);
+    const char* tb = (const char*)p.typed[kk];
+    const size_t coef_idx = coefs.size();
+    coefs.insert(coefs.end(), it.coef, it.coef + it.K + 1);
+    for (int col0 = 0; col0 < it.n_b; col0 += W) {
+      const int ncols = std::min(W, it.n_b - col0);
+      void* xs = base + slice_pos;
+      void* ba = base + slice_pos + sb;
+      void* bb = base + slice_pos + 2 * sb;
+      slice_pos += 3 * sb;
+      if (it.K == 0) {
+        PF_CHECK(slice_in(kind, abi_kind, it.in, g.dim, it.n_b, col0, ncols, W, nullptr, ba, nullptr,
+                          it.coef[0] * it.invD, flag, s));
+        continue;
+      }
+      PF_CHECK(slice_in(kind, abi_kind, it.in, g.dim, it.n_b, col0, ncols, W, xs, ba, bb, it.coef[it.K], flag, s));
+      BatchJob J{};
+      J.t = StepTables{p.tab.rec, p.tab.grec, tb, tb + ((size_t)1 << g.b) * cs,
+                       tb + (((size_t)1 << g.b) + ((size_t)1 << g.nh)) * cs, p.tab.order};
+      J.coef = (const double*)(base + Lo.coef_off) + coef_idx;
+      J.xs = xs;
+      J.ba = ba;
+      J.bb = bb;
+      J.invD = it.invD;
+      J.o1 = alpha * 0.5 * g.J1;
+      J.o2 = alpha * 0.5 * g.J2;
+      J.K = it.K;
+      J.n_groups = g.n_groups;
+      J.n_cross = g.n_cross;
+      J.nlo_tab = 1 << g.b;
+      for (int k = 0; k < g.n_cross && k < 6; k++) {
+        J.cross_lo[k] = g.cross_lo[k];
+        J.cross_cls[k] = g.cross_cls[k];
+      }
+      jobs.push_back(J);
+      n_steps = std::max(n_steps, it.K);
+      tile_elems = std::max(tile_elems, g.max_group * W);
+      nlo_max = std::max(nlo_max, 1 << g.b);
+      // Clenshaw minimum per step: read b_{k+1}, b_{k+2}, write b_k, read X when c_k != 0
+      for (int k = it.K - 1; k >= 0; k--) {
+        const bool hx = (k >= 1 ? it.coef[k] : it.coef[0]) != 0.0;
+        alg += (double)g.dim * W * es * (3.0 + (hx ? 1.0 : 0.0));
+      }
+    }
+  }
+  if (!jobs.empty()) {
+    PF_CUDA(cudaMemcpyAsync(base + Lo.coef_off, coefs.data(), coefs.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    PF_CUDA(cudaMemcpyAsync(base + Lo.jobs_off, jobs.data(), jobs.size() * sizeof(BatchJob), cudaMemcpyHostToDevice, s));
+    unsigned* bar = (unsigned*)(base + Lo.bar_off);
+    int* err = (int*)(bar + 2);
+    int grid = 0;
+    StepTimer tm(s);
+    int rc;
+    if (kind == POLFED_F32)
+      rc = j2 ? launch_batched<NF32, true>((const BatchJob*)base, (int)jobs.size(), n_steps, tile_elems, nlo_max, bar,
+                                           err, ctas_per_sm, s, &grid)
+              : launch_batched<NF32, false>((const BatchJob*)base, (int)jobs.size(), n_steps, tile_elems, nlo_max, bar,
+                                            err, ctas_per_sm, s, &grid);
+    else
+      rc = j2 ? launch_batched<NDF, true>((const BatchJob*)base, (int)jobs.size(), n_steps, tile_elems, nlo_max, bar,
+                                          err, ctas_per_sm, s, &grid)
+              : launch_batched<NDF, false>((const BatchJob*)base, (int)jobs.size(), n_steps, tile_elems, nlo_max, bar,
+                                           err, ctas_per_sm, s, &grid);
+    if (rc != POLFED_OK) return rc;
+    const double g0 = counters().step_gpu_s;
+    PF_CHECK(tm.stop());
+    Counters& cn = counters();
+    cn.step_launches++;
+    cn.step_alg_bytes += alg;
+    if (bst) {
+      bst->n_jobs = (int)jobs.size();
+      bst->n_steps = n_steps;
+      bst->grid = grid;
+      bst->gpu_s = cn.step_gpu_s - g0;
+      bst->alg_bytes = alg;
+    }
+    int e = 0;
+    PF_CUDA(cudaMemcpyAsync(&e, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PF_CUDA(cudaStreamSynchronize(s));
+    if (e) return fail(POLFED_ETIMEOUT, "a grid barrier of the batched filter timed out");
+  }
+  // outputs: the buffer written by each job's last step
+  slice_pos = Lo.slices_off;
+  for (size_t q = 0; q < items.size(); q++) {
+    BatchFilterItem& it = items[q];
+    const HamGeometry& g = it.plan->geo;
+    float* flag = (float*)(base + Lo.flags_off + 16 * q);
+    const size_t sb = ((size_t)g.dim * W * es + 255) & ~(size_t)255;
+    for (int col0 = 0; col0 < it.n_b; col0 += W) {
+      const int ncols = std::min(W, it.n_b - col0);
+      char* ba = base + slice_pos + sb;
+      char* bb = base + slice_pos + 2 * sb;
+      slice_pos += 3 * sb;
+      const void* res = it.K == 0 ? (const void*)ba : (((it.K - 1) & 1) ? (const void*)ba : (const void*)bb);
+      PF_CHECK(slice_out(kind, abi_kind, res, g.dim, W, ncols, it.out, it.n_b, col0, flag, s));
+    }
+  }
+  std::vector<float> fl(4 * items.size());
+  PF_CUDA(cudaMemcpyAsync(fl.data(), base + Lo.flags_off, 16 * items.size(), cudaMemcpyDeviceToHost, s));
+  PF_CUDA(cudaStreamSynchronize(s));
+  for (size_t q = 0; q < items.size(); q++) {
+    int bad = 0;
+    memcpy(&bad, &fl[4 * q + 2], 4);
+    double csum = 0.0;
+    for (int n = 0; n <= items[q].K; n++) csum += std::fabs(items[q].coef[n]);
+    const double bound = csum * items[q].invD * std::sqrt((double)items[q].plan->geo.dim) * fl[4 * q] * 1.01 + 1e-300;
+    items[q].bounds_error = bad || (double)fl[4 * q + 1] > bound;
+  }
   return POLFED_OK;
 }
 

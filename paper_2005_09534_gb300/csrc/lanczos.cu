@@ -85,7 +85,7 @@ struct polfed_ctx {
   size_t ws_limit = 0, ws_total = 0;
   polfed_opts opts;
   bool have_opts = false;
-  DevBuf basis, U, R, fscr, ritz, small, evbuf, work, vecs;
+  DevBuf basis, U, R, fscr, ritz, small, evbuf, work, vecs, kpm;
   Dense dense;
   polfed_stats last;
 };
@@ -193,12 +193,26 @@ struct LanczosParams {
   double tol_resid_t;  // acceptance threshold on ||H~ u - eps u||
   bool accept_any;     // accept the first verified set (FP32 stage before refinement)
   bool fill_panels;    // top the converged set up to whole panels (input of the refinement)
+  FilterHook* hook = nullptr;  // batched runner: filter calls go through it
 };
+
+// Y_q = invD sum_n coef[n] T_n(H~) X_q for the panels q (dim x S each), directly
+// or through the batched runner's rendezvous.
+int run_filter(HamPlan& plan, const LanczosParams& P, int kind, const double* coef, int K, double invD,
+               const double* const* in, double* const* out, int npan, int S, FilterScratch& scr, cudaStream_t s,
+               int lpr) {
+  if (P.hook && (kind == POLFED_F32 || kind == POLFED_DF64))
+    return P.hook->filter(plan, kind, coef, K, invD, in, out, npan, S, s);
+  for (int q = 0; q < npan; q++)
+    PF_CHECK(filter_block(plan, kind, coef, K, invD, in[q], out[q], S, POLFED_F64, scr, s, lpr));
+  return POLFED_OK;
+}
 
 struct LanczosOut {
   std::vector<double> evals_t;  // H~ units, ascending
   std::vector<double> resid_t;  // H~ units
   int n_out = 0, m = 0, n_conv = 0, checks = 0, ritz_cols = 0, n_refine = 0, refine_K = 0;
+  int n_acc = -1;  // Ritz values theta >= p at the last check (converged or not); -1 = no check yet
   int64_t matvec_cols = 0;
   double t_filter = 0, t_reorth = 0, t_qr = 0, t_teig = 0, t_ritz = 0;
 };
@@ -260,7 +274,11 @@ int run_lanczos(polfed_ctx* c, HamPlan& plan, const LanczosParams& P, double* d_
   for (int j = 0; j < m_max; j++) {
     double* Qj = Qb + (int64_t)j * pstride;
     double t0 = now_s();
-    PF_CHECK(filter_block(plan, kind, coef.data(), P.K, invD, Qj, Ub, S, POLFED_F64, scr, s, lpr));
+    {
+      const double* in1[1] = {Qj};
+      double* out1[1] = {Ub};
+      PF_CHECK(run_filter(plan, P, kind, coef.data(), P.K, invD, in1, out1, 1, S, scr, s, lpr));
+    }
     PF_CHECK(D.coldot(Ub, Ub, S, colnrm.data(), s));  // synchronizes
     out.matvec_cols += (int64_t)P.K * S;
     double t1 = now_s();
@@ -369,6 +387,8 @@ int run_lanczos(polfed_ctx* c, HamPlan& plan, const LanczosParams& P, double* d_
     for (int k = 0; k < std::min(n, P.N_ev); k++) maxres_top = std::max(maxres_top, tres[ord[k]]);
     const bool ok = ok_theta && maxres_top <= tol_cur;
     out.n_conv = nconv_p;
+    out.n_acc = 0;
+    for (int i = 0; i < n; i++) out.n_acc += theta[i] >= p;
     if (debug_on()) {
       fprintf(stderr, "[polfed dbg] check n=%d: top theta/res:", n);
       for (int k = 0; k < std::min(n, 12); k++) fprintf(stderr, " %.4f/%.1e", theta[ord[k]], tres[ord[k]]);
@@ -590,9 +610,15 @@ int refine(polfed_ctx* c, HamPlan& plan, const LanczosParams& P, int Kr, int nr,
   scr.xs = c->fscr.p;
   scr.bytes = c->fscr.n;
   const double t0 = now_s();
-  for (int q = 0; q < npan; q++)
-    PF_CHECK(filter_block(plan, POLFED_DF64, cf.data(), Kr, 1.0, U + (size_t)q * pstride, F + (size_t)q * pstride, S,
-                          POLFED_F64, scr, s, lpr));
+  {
+    std::vector<const double*> ins(npan);
+    std::vector<double*> outs(npan);
+    for (int q = 0; q < npan; q++) {
+      ins[q] = U + (size_t)q * pstride;
+      outs[q] = F + (size_t)q * pstride;
+    }
+    PF_CHECK(run_filter(plan, P, POLFED_DF64, cf.data(), Kr, 1.0, ins.data(), outs.data(), npan, S, scr, s, lpr));
+  }
   out.matvec_cols += (int64_t)Kr * nr;
   const double t1 = now_s();
   out.t_filter += t1 - t0;
@@ -691,6 +717,35 @@ int spectral_bounds(polfed_ctx* c, HamPlan& plan, const polfed_opts& o, double* 
   return POLFED_OK;
 }
 
+// Density of states per unit of H~ at sigma (whole sector) from the KPM
+// eigenvalue count of the window [sigma - d, sigma + d], d = max(0.01, 8 / n_mom)
+// (a few Jackson widths pi / n_mom), with R random vectors of seed.
+int kpm_rho(polfed_ctx* c, HamPlan& plan, double e_lo, double e_hi, double sigma, int n_mom, int R, uint64_t seed,
+            double* rho_t, int64_t* matvecs) {
+  cudaStream_t s = c->stream;
+  const int64_t dim = plan.geo.dim;
+  const int kind = POLFED_DF64;
+  PF_CHECK(plan.prepare_typed(kind, e_lo, e_hi));
+  const int lpr = choose_lpr(kind, R);
+  PF_CHECK(c->fscr.ensure(std::max(c->fscr.n, filter_scratch_bytes(plan, kind, lpr)), &c->ws_total, c->ws_limit));
+  FilterScratch scr;
+  scr.xs = c->fscr.p;
+  scr.bytes = c->fscr.n;
+  const size_t vb = ((size_t)dim * R * sizeof(double) + 255) & ~(size_t)255;
+  PF_CHECK(c->kpm.ensure(vb + kpm_buffer_bytes(dim, R, POLFED_F64), &c->ws_total, c->ws_limit));
+  double* r = c->kpm.as<double>();
+  PF_CHECK(c->dense.random_fill(r, dim * R, seed ^ 0x6b706d5f646f73ull, s));
+  const KpmBuffers b = kpm_carve((char*)c->kpm.p + vb, dim, R, POLFED_F64);
+  std::vector<double> mu(n_mom);
+  PF_CHECK(kpm_moments(plan, kind, r, R, n_mom, mu.data(), b, scr, s));
+  *matvecs += (int64_t)R * ((n_mom + 1) / 2);
+  const double d = std::max(0.01, 8.0 / n_mom);
+  const double xa = std::max(-1.0, sigma - d), xb = std::min(1.0, sigma + d);
+  const double f = kpm_count_fraction(mu.data(), n_mom, xa, xb);
+  *rho_t = std::max(f, 1e-12) * (double)dim / (xb - xa);
+  return POLFED_OK;
+}
+
 int moments(polfed_ctx* c, HamPlan& plan, double* mean, double* var) {
   cudaStream_t s = c->stream;
   PF_CHECK(c->small.ensure(std::max(c->small.n, (size_t)64), &c->ws_total, c->ws_limit));
@@ -754,6 +809,7 @@ void polfed_ctx_destroy(polfed_ctx* c) {
   c->evbuf.release();
   c->work.release();
   c->vecs.release();
+  c->kpm.release();
   c->dense.release();
   if (c->solver) cusolverDnDestroy(c->solver);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -822,6 +878,16 @@ int polfed_block_lanczos(polfed_ctx* c, const polfed_model* model, double e_lo, 
 
 int polfed_eigs(polfed_ctx* c, const polfed_model* model, double eps_target, int32_t N_ev, int32_t K, int32_t n_b,
                 const polfed_opts* opts, double* evals, double* d_evecs, double* resid, polfed_stats* stats) {
+  return polfed::eigs_impl(c, model, eps_target, N_ev, K, n_b, opts, evals, d_evecs, resid, stats, nullptr);
+}
+
+}  // extern "C"
+
+namespace polfed {
+
+int eigs_impl(polfed_ctx* c, const polfed_model* model, double eps_target, int32_t N_ev, int32_t K, int32_t n_b,
+              const polfed_opts* opts, double* evals, double* d_evecs, double* resid, polfed_stats* stats,
+              FilterHook* hook) {
   if (!c) return fail(POLFED_EINVAL, "ctx is NULL");
   if (!evals) return fail(POLFED_EINVAL, "evals is NULL");
   if (!(eps_target >= 0.0 && eps_target <= 1.0)) return fail(POLFED_EINVAL, "eps_target must be in [0, 1]");
@@ -841,7 +907,7 @@ int polfed_eigs(polfed_ctx* c, const polfed_model* model, double eps_target, int
   const double t0 = now_s();
   const Counters cn0 = counters();
   HamPlan plan;
-  PF_CHECK(plan.init(model, c->stream, false));
+  PF_CHECK(plan.init(model, c->stream, false, hook ? hook->plan_b(model->L) : -1));
   count_launch(4);  // table kernels
   const int64_t dim = plan.geo.dim;
   if (N_ev < 1 || N_ev > dim) return fail(POLFED_EINVAL, "N_ev must be in 1..dim");
@@ -853,17 +919,69 @@ int polfed_eigs(polfed_ctx* c, const polfed_model* model, double eps_target, int
   if (!(Emax > Emin)) return fail(POLFED_EINVAL, "degenerate spectrum (E_max == E_min)");
   const double width = Emax - Emin;
   const double pad = 1e-6 * width + 10.0 * berr;
-  const double e_lo = Emin - pad, e_hi = Emax + pad;
+  double e_lo = Emin - pad, e_hi = Emax + pad;
+  int bounds_from_hint = 0;
+  if (o.dos_rule == POLFED_DOS_HINT && o.emin_hint < o.emax_hint) {
+    // predicted bounds: kept only if the probe confirms they contain the
+    // spectrum (a bound inside it would make the recurrence grow) and they are
+    // not looser than 5% of the width
+    if (o.emin_hint <= Emin - 10.0 * berr && o.emax_hint >= Emax + 10.0 * berr &&
+        o.emax_hint - o.emin_hint <= 1.05 * width) {
+      e_lo = o.emin_hint;
+      e_hi = o.emax_hint;
+      bounds_from_hint = 1;
+    }
+  }
   const double Estar = Emin + eps_target * width;
   double sigma = (2.0 * Estar - e_lo - e_hi) / (e_hi - e_lo);
   if (std::fabs(sigma) < 1e-14) sigma = 0.0;
   if (!(sigma > -1.0 && sigma < 1.0)) return fail(POLFED_EINVAL, "target outside the spectrum");
   // 2. order K from the density of states at the target
-  double mean = 0, var = 0;
-  PF_CHECK(moments(c, plan, &mean, &var));
-  const double gam = std::sqrt(std::max(var, 1e-300));
-  const double rho = (double)dim / (std::sqrt(2.0 * M_PI) * gam) * std::exp(-0.5 * (Estar - mean) * (Estar - mean) / (gam * gam));
-  const double rho_t = rho * 0.5 * (e_hi - e_lo);
+  double mean = 0, var = 0, rho = 0.0, rho_t = 0.0;
+  switch (o.dos_rule) {
+    case POLFED_DOS_MOMENTS: {
+      PF_CHECK(moments(c, plan, &mean, &var));
+      const double gam = std::sqrt(std::max(var, 1e-300));
+      rho = (double)dim / (std::sqrt(2.0 * M_PI) * gam) * std::exp(-0.5 * (Estar - mean) * (Estar - mean) / (gam * gam));
+      rho_t = rho * 0.5 * (e_hi - e_lo);
+      break;
+    }
+    case POLFED_DOS_GAMMA: {
+      // analytic infinite-temperature width of Eq. (1) (Supplement: Gamma^2 =
+      // L [(1 + J2^2)/8 + Delta^2 (1 + J2^2)/16 + W^2/12] for J1 = 1), per
+      // realization (sum h_i^2 / 4 in place of L W^2 / 12) and per bond count
+      // (nb_l terms of class l), centred at the exact sector mean: in the
+      // S^z = 0 sector <S^z_i S^z_j> = -1 / (4 (L - 1)) for i != j.
+      const polfed_model& md = *model;
+      const double nb1 = md.periodic ? md.L : md.L - 1, nb2 = md.periodic ? md.L : md.L - 2;
+      double hh = 0.0;
+      for (int i = 0; i < md.L; i++) hh += md.h[i] * md.h[i];
+      var = (nb1 * md.J1 * md.J1 + nb2 * md.J2 * md.J2) * (1.0 / 8.0 + md.Delta * md.Delta / 16.0) + hh / 4.0;
+      mean = -md.Delta * (nb1 * md.J1 + nb2 * md.J2) / (4.0 * (md.L - 1));
+      const double gam = std::sqrt(var);
+      rho = (double)dim / (std::sqrt(2.0 * M_PI) * gam) * std::exp(-0.5 * (Estar - mean) * (Estar - mean) / (gam * gam));
+      rho_t = rho * 0.5 * (e_hi - e_lo);
+      break;
+    }
+    case POLFED_DOS_KPM: {
+      const int nm = o.kpm_moments > 0 ? o.kpm_moments : 256;
+      const int nv = o.kpm_vectors > 0 ? o.kpm_vectors : 16;
+      if (nm < 16 || nm > kMaxKpmMoments || nv > 128) return fail(POLFED_EINVAL, "bad kpm_moments / kpm_vectors");
+      PF_CHECK(kpm_rho(c, plan, e_lo, e_hi, sigma, nm, nv, o.seed, &rho_t, &mv));
+      rho = rho_t / (0.5 * (e_hi - e_lo));
+      break;
+    }
+    case POLFED_DOS_HINT: {
+      if (!(o.rho_hint > 0.0) || !std::isfinite(o.rho_hint)) return fail(POLFED_EINVAL, "rho_hint must be > 0");
+      rho = o.rho_hint * (double)dim / width;
+      rho_t = rho * 0.5 * (e_hi - e_lo);
+      break;
+    }
+    default:
+      return fail(POLFED_EINVAL, "bad opts.dos_rule");
+  }
+  const double gam = std::sqrt(std::max(var, 0.0));
+  const int K_auto = (K == 0);
   if (K == 0) {
     const double y = lobe_root(o.p);
     const double n_target = (1.0 + o.k_margin) * N_ev;
@@ -880,18 +998,50 @@ int polfed_eigs(polfed_ctx* c, const polfed_model* model, double eps_target, int
   const double hnorm0 = std::max(std::fabs(Emin), std::fabs(Emax));
   const bool mixed = o.precision == POLFED_F32;
   LanczosParams P{e_lo, e_hi, sigma, K, S, N_ev, o, o.tol_resid * hnorm0 / (0.5 * (e_hi - e_lo)), mixed, false};
+  P.hook = hook;
   if (mixed) P.o.tol_conv = std::max(o.tol_conv, 2e-5);  // FP32 filter: stop at its noise floor
   LanczosOut lo;
-  int rc = run_lanczos(c, plan, P, d_evecs, lo);
+  int rc = POLFED_OK, restarts = 0;
+  for (;;) {
+    LanczosOut cur;
+    rc = run_lanczos(c, plan, P, d_evecs, cur);
+    if (restarts > 0) {  // the work of the abandoned attempts still counts
+      cur.matvec_cols += lo.matvec_cols;
+      cur.checks += lo.checks;
+      cur.t_filter += lo.t_filter;
+      cur.t_reorth += lo.t_reorth;
+      cur.t_qr += lo.t_qr;
+      cur.t_teig += lo.t_teig;
+      cur.t_ritz += lo.t_ritz;
+    }
+    lo = std::move(cur);
+    if (rc != POLFED_ENOCONV || K_auto == 0 || restarts >= 2 || lo.n_acc < 0 || lo.n_acc >= N_ev) break;
+    // Fewer than N_ev eigenvalues have P >= p: the density of states was
+    // overestimated and K is too large for the window to hold N_ev.  Shrink K
+    // so that the window holds about (1 + k_margin) N_ev of the values seen.
+    const double f = std::max(0.25, 0.9 * std::max(lo.n_acc, 1) / ((1.0 + o.k_margin) * N_ev));
+    int Kn = std::min((int)(K * f), (int)(0.8 * K));
+    if (sigma == 0.0) Kn &= ~1;
+    Kn = std::max(2, Kn);
+    if (o.verbose || debug_on())
+      fprintf(stderr, "[polfed] %d accessible eigenvalues < N_ev = %d: restart with K %d -> %d\n", lo.n_acc, N_ev, K,
+              Kn);
+    K = Kn;
+    P.K = K;
+    restarts++;
+  }
   if (rc != POLFED_OK && rc != POLFED_ENOCONV) return rc;
   if (mixed && lo.n_out > 0) {
     // refinement sweeps with a float-float filter until the residuals pass
     int Kr = std::max(16, K / 2);
     if (sigma == 0.0) Kr &= ~1;
-    for (int sweep = 0; sweep < 3; sweep++) {
+    double mr_prev = 1e300;
+    for (int sweep = 0; sweep < 6; sweep++) {
       double mr = 0.0;
       for (double r : lo.resid_t) mr = std::max(mr, r);
       if (lo.n_out >= N_ev && mr <= P.tol_resid_t && sweep > 0) break;
+      if (sweep >= 3 && mr > 0.5 * mr_prev) break;  // stagnating: more sweeps will not help
+      mr_prev = mr;
       if (o.verbose || debug_on())
         fprintf(stderr, "[polfed] refinement sweep %d: Kr %d, max resid (H~) before %.3e\n", sweep + 1, Kr, mr);
       const double tr0 = now_s();
@@ -935,6 +1085,9 @@ int polfed_eigs(polfed_ctx* c, const polfed_model* model, double eps_target, int
   st.target = Estar;
   st.rho_sigma = rho_t;
   st.t_bounds = t_b;
+  st.n_restarts = restarts;
+  st.dos_rule = o.dos_rule;
+  st.bounds_from_hint = bounds_from_hint;
   st.t_filter = lo.t_filter;
   st.t_reorth = lo.t_reorth;
   st.t_qr = lo.t_qr;
@@ -951,6 +1104,52 @@ int polfed_eigs(polfed_ctx* c, const polfed_model* model, double eps_target, int
   if (rc == POLFED_OK && st.max_resid > o.tol_resid * hnorm && o.verbose)
     fprintf(stderr, "[polfed] warning: max residual %.3e exceeds tol %.3e\n", st.max_resid, o.tol_resid * hnorm);
   return rc;
+}
+
+}  // namespace polfed
+
+extern "C" {
+
+int polfed_spectral_bounds(polfed_ctx* c, const polfed_model* model, double* bounds) {
+  if (!c) return fail(POLFED_EINVAL, "ctx is NULL");
+  if (!bounds) return fail(POLFED_EINVAL, "bounds is NULL");
+  ScopedDevice sd(c->device);
+  HamPlan plan;
+  PF_CHECK(plan.init(model, c->stream, false));
+  polfed_opts o = c->opts;
+  if (!c->have_opts) polfed_opts_default(&o);
+  int64_t mv = 0;
+  PF_CHECK(spectral_bounds(c, plan, o, &bounds[0], &bounds[1], &bounds[2], &mv));
+  return POLFED_OK;
+}
+
+int polfed_spectral_labels(polfed_ctx* c, const polfed_model* model, double eps_target, int32_t n_mom, int32_t R,
+                           double* out) {
+  if (!c) return fail(POLFED_EINVAL, "ctx is NULL");
+  if (!out) return fail(POLFED_EINVAL, "out is NULL");
+  if (!(eps_target > 0.0 && eps_target < 1.0)) return fail(POLFED_EINVAL, "eps_target must be in (0, 1)");
+  if (n_mom < 16 || n_mom > kMaxKpmMoments) return fail(POLFED_EINVAL, "n_mom must be in 16..65536");
+  if (R < 1 || R > 128) return fail(POLFED_EINVAL, "R must be in 1..128");
+  ScopedDevice sd(c->device);
+  HamPlan plan;
+  PF_CHECK(plan.init(model, c->stream, false));
+  polfed_opts o = c->opts;
+  if (!c->have_opts) polfed_opts_default(&o);
+  double Emin = 0, Emax = 0, berr = 0;
+  int64_t mv = 0;
+  PF_CHECK(spectral_bounds(c, plan, o, &Emin, &Emax, &berr, &mv));
+  if (!(Emax > Emin)) return fail(POLFED_EINVAL, "degenerate spectrum (E_max == E_min)");
+  const double width = Emax - Emin;
+  const double pad = 1e-6 * width + 10.0 * berr;
+  const double e_lo = Emin - pad, e_hi = Emax + pad;
+  const double Estar = Emin + eps_target * width;
+  const double sigma = (2.0 * Estar - e_lo - e_hi) / (e_hi - e_lo);
+  double rho_t = 0.0;
+  PF_CHECK(kpm_rho(c, plan, e_lo, e_hi, sigma, n_mom, R, o.seed, &rho_t, &mv));
+  out[0] = Emin;
+  out[1] = Emax;
+  out[2] = rho_t / (0.5 * (e_hi - e_lo)) * width / (double)plan.geo.dim;
+  return POLFED_OK;
 }
 
 }  // extern "C"

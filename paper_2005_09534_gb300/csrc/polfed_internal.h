@@ -163,8 +163,62 @@ int apply_block(HamPlan& plan, int kind, const void* in, void* out, int n_b, int
 size_t filter_scratch_bytes(const HamPlan& plan, int kind, int lpr);
 int choose_lpr(int kind, int n_b);
 
+// Batched filter: one cooperative launch runs the Clenshaw recurrences of
+// many (realization, 128-byte column slice) jobs, each with its own plan,
+// order and coefficients (F32 or DF64 storage; all jobs J2 == 0 or all not).
+struct BatchFilterItem {
+  HamPlan* plan;          // prepare_typed(kind, ...) done
+  const double* coef;     // host, K + 1 coefficients: Y = invD * sum_n coef[n] T_n(H~) X
+  int K;
+  double invD;
+  const void* in;         // device, row-major dim x n_b (abi kind)
+  void* out;              // device, row-major dim x n_b
+  int n_b;
+  bool bounds_error;      // out: output grew beyond the Chebyshev bound
+};
+struct BatchStats {
+  int n_jobs = 0, n_steps = 0, grid = 0;
+  double gpu_s = 0.0, alg_bytes = 0.0;
+};
+size_t batch_scratch_bytes(const std::vector<BatchFilterItem>& items, int kind);
+int filter_batched(std::vector<BatchFilterItem>& items, int kind, int abi_kind, void* scratch, size_t bytes,
+                   cudaStream_t s, int ctas_per_sm, BatchStats* st);
+
+// Filter calls of the block-Lanczos driver can be routed through a hook (the
+// batched runner's rendezvous).  Panels q = 0..npan-1: out[q] = invD sum_n
+// coef[n] T_n(H~) in[q], each dim x S row-major FP64 on `s`.
+struct FilterHook {
+  virtual int filter(HamPlan& plan, int kind, const double* coef, int K, double invD, const double* const* in,
+                     double* const* out, int npan, int S, cudaStream_t s) = 0;
+  virtual int plan_b(int L) { return -1; }  // low/high split for the plans (-1 = default)
+  virtual ~FilterHook() {}
+};
+// polfed_eigs with an optional hook (nullptr = direct filter launches).
+int eigs_impl(polfed_ctx* c, const polfed_model* model, double eps_target, int32_t N_ev, int32_t K, int32_t n_b,
+              const polfed_opts* opts, double* evals, double* d_evecs, double* resid, polfed_stats* stats,
+              FilterHook* hook);
+
 // Chebyshev coefficients of Eq. (2) in FP64: c_n, n = 0..K, and D.
 void cheb_coeffs(double sigma, int K, std::vector<double>& c, double& D);
+
+// Kernel polynomial method: stochastic Chebyshev moments of H~ and the
+// Jackson-damped fraction of the spectrum inside an interval.
+constexpr int kMaxKpmMoments = 65536;
+struct KpmBuffers {
+  void* t0;
+  void* t1;
+  void* y;       // three dim x R blocks of the ABI element type
+  double* part;  // per-block partial sums
+  double* mu;    // raw moment pairs
+};
+void jackson_coeffs(int N, std::vector<double>& g);
+size_t kpm_buffer_bytes(int64_t dim, int R, int abi_kind);
+KpmBuffers kpm_carve(void* base, int64_t dim, int R, int abi_kind);
+// mu[n] = (1/R) sum_r r^T T_n(H~) r, n < n_mom (host out); r is row-major dim x R
+// of float (kind POLFED_F32) or double.  Needs plan.prepare_typed(kind, ...).
+int kpm_moments(HamPlan& plan, int kind, const void* r, int R, int n_mom, double* mu, const KpmBuffers& b,
+                FilterScratch& scr, cudaStream_t s);
+double kpm_count_fraction(const double* mu, int n_mom, double x_a, double x_b);
 
 // Basis kernel (polfed_basis_build).
 int launch_basis(int L, int n_up, uint32_t* d_states, int64_t dim, cudaStream_t s);

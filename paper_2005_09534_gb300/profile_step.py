@@ -1,0 +1,39 @@
+"""One small filter call for kernel profiling (run under ncu).
+
+  python -m paper_2005_09534_gb300.profile_step [F32|DF64|F64] [L] [n_b] [K]
+
+Filters a seeded block through P^K (sigma = 0) of the L-site XXZ chain with
+W = 3 fields: K + 1 step-kernel launches per 128-byte column slice, so
+`ncu -k regex:k_ham_step -s 3 -c 1` captures one full-size step launch.
+"""
+import sys
+
+import torch
+
+import polfed_inputs as I
+
+from . import DF64, F32, F64, basis_build, cheb_filter, load
+
+
+def main(argv):
+    kind = argv[1] if len(argv) > 1 else "F32"
+    L = int(argv[2]) if len(argv) > 2 else 22
+    nb = int(argv[3]) if len(argv) > 3 else 64
+    K = int(argv[4]) if len(argv) > 4 else 6
+    dt = {"F32": (F32, torch.float32), "DF64": (DF64, torch.float64), "F64": (F64, torch.float64)}[kind]
+    load()
+    dev = torch.device("cuda:0")
+    m = I.xxz(L, 3.0, 4, 0)
+    dim = basis_build(L, L // 2)
+    st = torch.empty(dim, dtype=torch.int32, device=dev)
+    basis_build(L, L // 2, st)
+    X = torch.from_numpy(I.block(dim, nb, 7)).to(dev, dt[1])
+    Y = torch.empty_like(X)
+    bound = 1.5 * (L * 1.25 + L * 3.0 / 2)  # > ||H||: bonds (1/2 + 1/4) each, fields |h_i|/2 <= 3/2
+    cheb_filter(m, st, dim, -bound, bound, 0.0, K, X, Y, nb, dt[0])
+    torch.cuda.synchronize()
+    print("profile_step ok", kind, L, dim, nb, K)
+
+
+if __name__ == "__main__":
+    main(sys.argv)

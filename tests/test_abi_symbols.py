@@ -52,9 +52,27 @@ def test_binding_loads_and_reports_errors_without_gpu(lib):
     assert e.value.code == pf.POLFED_EINVAL
 
 
-def test_struct_layouts_match_header():
+def test_struct_layouts_match_header(tmp_path):
+    """Every field of the ctypes mirrors sits at the offset the C compiler gives it."""
+    import subprocess
     import paper_2005_09534_gb300 as pf
-    # polfed_model: int32, int32, 3 doubles, pointer; opts: 5 doubles, 4 int32, uint64
-    assert ctypes.sizeof(pf.CModel) == 8 + 24 + 8
-    assert ctypes.sizeof(pf.COpts) == 40 + 16 + 8
-    assert ctypes.sizeof(pf.CStats) == 8 * 4 + 2 * 8 + 15 * 8 + 2 * 8 + 2 * 8
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    structs = [("polfed_model", pf.CModel), ("polfed_opts", pf.COpts), ("polfed_stats", pf.CStats),
+               ("polfed_batch_info", pf.CBatchInfo)]
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "polfed.h"', "int main(void) {"]
+    for cname, cls in structs:
+        lines.append(f'  printf("{cname} %zu\\n", sizeof({cname}));')
+        for f, _ in cls._fields_:
+            lines.append(f'  printf("{cname}.{f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                 text=True).stdout.splitlines())
+    for cname, cls in structs:
+        assert int(got[cname]) == ctypes.sizeof(cls), cname
+        for f, _ in cls._fields_:
+            assert int(got[f"{cname}.{f}"]) == getattr(cls, f).offset, f"{cname}.{f}"
