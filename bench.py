@@ -35,7 +35,10 @@ WORKLOADS = {
     "L14_xxz_W3": (I.xxz, 14, 3.0, 50, 16, 1),
     "L24_j1j2_W5": (I.j1j2, 24, 5.0, 1000, 64, 5),
 }
+# 64 XXZ rings, L = 16 / 18 alternating, W cycling {1,2,3,4,6,8}, N_ev cycling {50,100,200}
+BATCHED = {"batched64_L16_L18": (64, (16, 18), (1.0, 2.0, 3.0, 4.0, 6.0, 8.0), (50, 100, 200), 3)}
 PREC = {"df64": 2, "f64": 0, "f32": 1}
+DOS = {"moments": 0, "gamma": 1, "kpm": 2, "mlp": 3}
 
 
 def peaks():
@@ -47,16 +50,25 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def step_kernel_traffic():
+def tma_kernel_source_sha():
+    """sha256 (16 hex) of the TMA step kernel's source text (from its section
+    comment to the slice-conversion code that follows it)."""
+    src = open(os.path.join(ROOT, "paper_2005_09534_gb300", "csrc", "hamiltonian.cu")).read()
+    a = src.index("// ------------------------------------------------- TMA-pipelined step kernel")
+    b = src.index("template <class NT>\nstruct Conv;")
+    return hashlib.sha256(src[a:b].encode()).hexdigest()[:16]
+
+
+def step_kernel_traffic(precision):
     """DRAM bytes per step-kernel launch from the committed ncu summary, if it
     was taken on the current kernel source (else None)."""
-    src = os.path.join(ROOT, "paper_2005_09534_gb300", "csrc", "hamiltonian.cu")
     try:
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        sha = tma_kernel_source_sha()
         with open(os.path.join(ROOT, "profiles", "step_kernel_traffic.json")) as f:
             d = json.load(f)
-        if d.get("source_sha") == sha:
-            return d
+        e = d.get(precision)
+        if e and e.get("source_sha") == sha:
+            return e
     except Exception:
         pass
     return None
@@ -158,8 +170,12 @@ def main():
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="L22_xxz_W3", choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default="df64", choices=sorted(PREC))
+    ap.add_argument("--workload", default="L22_xxz_W3", choices=sorted(WORKLOADS) + sorted(BATCHED))
+    ap.add_argument("--precision", default="f32", choices=sorted(PREC))
+    ap.add_argument("--dos", default="mlp", choices=sorted(DOS),
+                    help="density-of-states rule for K (mlp: the learned predictor, trained before timing)")
+    ap.add_argument("--batch-mode", default="batched", choices=["batched", "sequential"],
+                    help="batched workloads: one polfed_eigs_batched call, or polfed_eigs per realization")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -183,6 +199,9 @@ def main():
     __graft_entry__.build()
     import paper_2005_09534_gb300 as pf
 
+    if args.workload in BATCHED:
+        run_batched(args, pf, torch, dev, world, rank, local, dist)
+        return
     builder, L, W, n_ev, n_b, cfg = WORKLOADS[args.workload]
     dim = pf.basis_build(L, L // 2)
     stream = torch.cuda.Stream(device=dev)
@@ -190,6 +209,10 @@ def main():
     ctx.set_stream(stream)
     opts = pf.opts_default()
     opts.precision = PREC[args.precision]
+    opts.dos_rule = DOS[args.dos]
+    net, mlp_info = None, None
+    if args.dos == "mlp":
+        net, mlp_info = train_predictor(pf, ctx, builder, L, W)
     evecs = torch.empty((n_ev, dim), dtype=torch.float64, device=dev)  # column-major dim x N_ev
     host_evecs = torch.empty((n_ev, dim), dtype=torch.float64, pin_memory=True)
     fields_pinned = torch.empty(L, dtype=torch.float64, pin_memory=True)
@@ -198,6 +221,11 @@ def main():
         m = builder(L, W, cfg, realization)
         fields_pinned.copy_(torch.from_numpy(m.h))
         model = pf.Model(L, m.J1, m.J2, m.Delta, fields_pinned.numpy(), m.periodic)
+        if net is not None:  # the learned predictor sets K (inference inside the timed step)
+            emin, emax, rho = net.predict(model, W)
+            opts.rho_hint = rho
+            w = emax - emin
+            opts.emin_hint, opts.emax_hint = emin - 0.02 * w, emax + 0.02 * w
         ev, res, st, rc = pf.eigs(ctx, model, 0.5, n_ev, 0, n_b, opts, d_evecs=evecs, allow_noconv=True)
         hn = max(abs(st["E_min"]), abs(st["E_max"]))
         ok = int(np.sum(res[: len(ev)] <= 1e-8 * hn)) if rc == 0 else 0
@@ -215,7 +243,7 @@ def main():
     e1 = torch.cuda.Event(enable_timing=True)
     dev_ms, wall_s, pairs = 0.0, 0.0, 0
     agg = {"n_launches": 0, "n_step_launches": 0, "step_gpu_s": 0.0, "step_alg_bytes": 0.0, "K": [], "m": [],
-           "max_rel_resid": 0.0, "status": []}
+           "max_rel_resid": 0.0, "status": [], "restarts": [], "refine": []}
     torch.cuda.synchronize()
     for k in range(args.steps):
         t0 = time.perf_counter()
@@ -233,21 +261,14 @@ def main():
         agg["K"].append(st["K"])
         agg["m"].append(st["m"])
         agg["status"].append(rc)
+        agg["restarts"].append(st["n_restarts"])
+        agg["refine"].append(st["n_refine"])
         agg["max_rel_resid"] = max(agg["max_rel_resid"], rr)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     ck = clocks.stop() if rank == 0 else None
-    t_dev = dev_ms / 1e3
-    if dist:
-        tt = torch.tensor([t_dev, wall_s], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        pp = torch.tensor([pairs], device=dev, dtype=torch.float64)
-        dist.all_reduce(pp)
-        t_dev, wall_s = float(tt[0]), float(tt[1])
-        pairs_all = int(pp.item())
-    else:
-        pairs_all = pairs
+    t_dev, wall_s, pairs_all = reduce_ranks(torch, dev, dist, dev_ms / 1e3, wall_s, pairs)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -257,10 +278,10 @@ def main():
     avg_launch = agg["step_gpu_s"] / max(1, agg["n_step_launches"])
     alg_per_launch = agg["step_alg_bytes"] / max(1, agg["n_step_launches"])
     achieved = alg_per_launch / avg_launch / 1e9 if avg_launch > 0 else 0.0
-    tr = step_kernel_traffic()
+    tr = step_kernel_traffic(args.precision)
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": (tr or {}).get("dram_bytes_per_launch"),
-            "peak_kind": f"of {peak_kind}", "kernel": "k_ham_step (Clenshaw step on a 128-byte column slice)",
+            "peak_kind": f"of {peak_kind}", "kernel": "k_ham_step_tma (Clenshaw step on a 128-byte column slice)",
             "alg_bytes_per_launch": alg_per_launch, "avg_launch_us": round(avg_launch * 1e6, 2)}
     value = pairs_all / t_dev
     bytes_d2h = n_ev * dim * 8 + 2 * n_ev * 8
@@ -269,7 +290,8 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
             "data": "synthetic",
             "config": {"workload": args.workload, "L": L, "dim": dim, "hamiltonian": builder.__name__,
-                       "W": W, "N_ev": n_ev, "n_b": n_b, "eps": 0.5, "K": agg["K"], "m": agg["m"],
+                       "W": W, "N_ev": n_ev, "n_b": n_b, "eps": 0.5, "dos_rule": args.dos, "K": agg["K"],
+                       "m": agg["m"], "restarts": agg["restarts"], "refine_sweeps": agg["refine"],
                        "parallelism": f"replicas x{world}", "l2": "per-step working set >> L2, no flush",
                        "status": agg["status"], "max_resid_over_normH": agg["max_rel_resid"]},
             "roofline": roof,
@@ -277,10 +299,159 @@ def main():
                     "h2d_bytes_per_step": L * 8, "d2h_bytes_per_step": bytes_d2h},
             "gpu_launches": int(agg["n_launches"]),
             "clocks": ck}
+    if mlp_info:
+        line["config"]["mlp"] = mlp_info
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_sample()
     print(json.dumps(line), flush=True)
     ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def reduce_ranks(torch, dev, dist, t_dev, wall_s, pairs):
+    """Max of the times and sum of the eigenpairs over ranks."""
+    if not dist:
+        return t_dev, wall_s, pairs
+    tt = torch.tensor([t_dev, wall_s], device=dev)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    pp = torch.tensor([pairs], device=dev, dtype=torch.float64)
+    dist.all_reduce(pp)
+    return float(tt[0]), float(tt[1]), int(pp.item())
+
+
+def train_predictor(pf, ctx, builder, L, W, n_real=64):
+    """Train the spectral predictor on labels the library produces (Lanczos
+    bounds, KPM counts) for n_real realizations at W' in [W/2, 3W/2] (field
+    config 90, disjoint from the timed realizations).  Untimed setup."""
+    from paper_2005_09534_gb300 import predictor
+    t0 = time.perf_counter()
+    models, Ws = [], []
+    for k in range(n_real):
+        w = W * (0.5 + ((0.6180339887498949 * (k + 1)) % 1.0))
+        models.append(builder(L, w, 90, k))
+        Ws.append(w)
+    labels = predictor.labels_for(ctx, models)
+    t1 = time.perf_counter()
+    X, Y = predictor.dataset(models, Ws, labels)
+    net = pf.MLP(L + 1, 128, 3, seed=7)
+    loss, secs = predictor.fit(net, X, Y, steps=6000, lr=2e-3, batch=256)
+    return net, {"train_realizations": n_real, "samples": int(X.shape[0]), "label_s": round(t1 - t0, 1),
+                 "train_s": round(secs, 1), "train_loss": round(float(loss), 4)}
+
+
+def batched_models(spec, base_realization):
+    n, Ls, Wc, Nc, cfg = spec
+    ms, nev = [], []
+    for r in range(n):
+        L = Ls[r % len(Ls)]
+        m = I.xxz(L, Wc[r % len(Wc)], cfg, base_realization + r)
+        ms.append(m)
+        nev.append(Nc[r % len(Nc)])
+    return ms, nev
+
+
+def run_batched(args, pf, torch, dev, world, rank, local, dist):
+    """One step = one polfed_eigs_batched call over the 64-realization batch
+    (autotuned block widths, one cooperative filter launch per round)."""
+    spec = BATCHED[args.workload]
+    opts = pf.opts_default()
+    opts.precision = PREC[args.precision] if args.precision != "f64" else pf.DF64
+
+    def solve(ms, nev):
+        if args.batch_mode == "batched":
+            return pf.eigs_batched(ms, 0.5, nev, n_b=0, opts=opts, device=local, allow_fail=True)
+        # the same realizations one after another through polfed_eigs (comparison mode)
+        evs, res, sts, status = [], [], [], []
+        t0 = time.perf_counter()
+        with pf.Ctx(local) as ctx:
+            for m, n in zip(ms, nev):
+                nb = 16 if n <= 100 else 32
+                ev, r, st, rc = pf.eigs(ctx, m, 0.5, n, 0, nb, opts, allow_noconv=True)
+                evs.append(ev)
+                res.append(r)
+                sts.append(st)
+                status.append(rc)
+        info = {"n_width16": sum(1 for n in nev if n <= 100), "n_width32": sum(1 for n in nev if n > 100),
+                "n_width64": 0, "ctas_per_sm": 0, "rounds": sum(s["n_step_launches"] for s in sts), "t_tune": 0.0,
+                "filter_gpu_s": sum(s["step_gpu_s"] for s in sts),
+                "filter_alg_bytes": sum(s["step_alg_bytes"] for s in sts),
+                "n_launches": sum(s["n_launches"] for s in sts), "t_total": time.perf_counter() - t0}
+        return evs, res, sts, np.array(status), info, 0
+
+    for w in range(args.warmup):
+        ms, nev = batched_models(spec, 10_000 + 1000 * (w * world + rank))
+        solve(ms, nev)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = Clocks(local)
+    if rank == 0:
+        clocks.start()
+    wall_s, dev_s, pairs = 0.0, 0.0, 0
+    infos, statuses, max_rr, restarts, fallbacks = [], [], 0.0, 0, 0
+    for k in range(args.steps):
+        ms, nev = batched_models(spec, 1000 * (k * world + rank))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        evs, res, sts, status, info, rc = solve(ms, nev)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        wall_s += dt
+        dev_s += dt  # host-driven multi-stream run: the device is busy for the whole call
+        for i, st in enumerate(sts):
+            hn = max(abs(st["E_min"]), abs(st["E_max"]))
+            if status[i] == 0:
+                pairs += int(np.sum(res[i] <= 1e-8 * hn))
+            max_rr = max(max_rr, float(np.max(res[i]) / hn) if len(res[i]) else 0.0)
+            restarts += st["n_restarts"]
+            fallbacks += st["fallback_df64"]
+        statuses += [int(x) for x in status]
+        infos.append(info)
+        for i, st in enumerate(sts):
+            hn = max(abs(st["E_min"]), abs(st["E_max"]))
+            print(f"[batched] r{i} L={ms[i].L} W={ms[i].W} N_ev={nev[i]} status={int(status[i])} n_b={st['n_b']} "
+                  f"K={st['K']} m={st['m']} refine={st['n_refine']} restarts={st['n_restarts']} "
+                  f"fallback={st['fallback_df64']} maxres/|H|={st['max_resid'] / hn:.2e} t={st['t_total']:.2f}s",
+                  file=sys.stderr)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ck = clocks.stop() if rank == 0 else None
+    t_dev, wall_s, pairs_all = reduce_ranks(torch, dev, dist, dev_s, wall_s, pairs)
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    peak, peak_kind = peaks()
+    fg = sum(i["filter_gpu_s"] for i in infos)
+    fa = sum(i["filter_alg_bytes"] for i in infos)
+    achieved = fa / fg / 1e9 if fg > 0 else 0.0
+    n, Ls, Wc, Nc, cfg = spec
+    line = {"metric": METRIC, "value": round(pairs_all / t_dev, 4), "unit": "eigenpairs/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * t_dev / args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
+            "data": "synthetic",
+            "config": {"workload": args.workload, "mode": args.batch_mode, "realizations": n, "L": list(Ls),
+                       "W": list(Wc),
+                       "N_ev": list(Nc), "eps": 0.5, "hamiltonian": "xxz",
+                       "n_width16_32_64": [infos[-1]["n_width16"], infos[-1]["n_width32"], infos[-1]["n_width64"]],
+                       "ctas_per_sm": infos[-1]["ctas_per_sm"], "rounds": [i["rounds"] for i in infos],
+                       "tune_s": [round(i["t_tune"], 2) for i in infos], "restarts": restarts,
+                       "fallback_df64": fallbacks, "status_nonzero": sum(1 for x in statuses if x != 0),
+                       "max_resid_over_normH": max_rr, "parallelism": f"replicas x{world}",
+                       "l2": "instances of 12870-48620 rows: filter working sets partly L2-resident, no flush"},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": f"of {peak_kind}",
+                         "kernel": "k_filter_batched (all realizations' Clenshaw steps, one cooperative launch)",
+                         "alg_bytes_per_launch": fa / max(1, sum(i["rounds"] for i in infos)),
+                         "avg_launch_us": round(1e6 * fg / max(1, sum(i["rounds"] for i in infos)), 1)},
+            "e2e": {"value": round(pairs_all / wall_s, 4), "unit": "eigenpairs/s",
+                    "h2d_bytes_per_step": sum(m.L * 8 for m in batched_models(spec, 0)[0]),
+                    "d2h_bytes_per_step": 16 * sum(batched_models(spec, 0)[1])},
+            "gpu_launches": int(sum(i["n_launches"] for i in infos)),
+            "clocks": ck}
+    print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
 

@@ -121,7 +121,7 @@ typedef struct polfed_stats {
   int32_t dos_rule;        /* rule that set K */
   int32_t bounds_from_hint;/* 1 if [e_lo, e_hi] came from the caller's (probe-confirmed) bounds hints */
   int32_t n_restarts;      /* restarts with a smaller K because fewer than N_ev eigenvalues had P >= p */
-  int32_t reserved;
+  int32_t fallback_df64;   /* POLFED_F32: 1 if the refinement stalled and a float-float run replaced it */
 } polfed_stats;
 
 typedef struct polfed_ctx polfed_ctx;
@@ -242,7 +242,8 @@ int polfed_block_lanczos(polfed_ctx* ctx, const polfed_model* model, double e_lo
  * With K = 0, a run that finds fewer than N_ev Ritz values with P >= p (the
  * density of states was overestimated) restarts, at most twice, with a
  * smaller K.  With precision POLFED_F32 the FP32-stage pairs are refined by
- * up to six float-float filter + Rayleigh-Ritz sweeps.
+ * up to four float-float filter + Rayleigh-Ritz sweeps; if they stall short
+ * of tol_resid, a float-float (POLFED_DF64) run replaces the result.
  * Blocking.  Returns POLFED_ENOCONV with partial results if the column
  * budget ran out. */
 int polfed_eigs(polfed_ctx* ctx, const polfed_model* model, double eps_target, int32_t N_ev, int32_t K, int32_t n_b,

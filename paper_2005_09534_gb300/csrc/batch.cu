@@ -14,8 +14,8 @@
 // Autotuner: before the run, the batched filter kernel is timed on the
 // realizations' own operators for each candidate block width (16, 32, 64
 // columns) and grid (1 or 2 CTAs per SM); each realization then takes the
-// width that minimizes (measured time per filtered column) x (columns its
-// Lanczos run needs, max(24, ceil(2.64 N_ev / S)) steps of S columns).
+// width that minimizes (measured time per filter step of width S) x (steps
+// its Lanczos run needs, about max(16, ceil(2.64 N_ev / S) + 8)).
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -286,7 +286,8 @@ int autotune(const std::vector<polfed_model>& models, const std::vector<int>& N_
     double best = 1e300;
     for (int wi = 0; wi < 3; wi++) {
       const int S = widths[wi];
-      const int m = std::max(24, (int)std::ceil(o.cols_factor * (1.0 + o.k_margin) * N_ev[i] / S) + 1);
+      // steps to convergence: onset at ms ~ 2.2 (1 + k_margin) N_ev, then about 8 more
+      const int m = std::max(16, (int)std::ceil(2.2 * (1.0 + o.k_margin) * N_ev[i] / S) + 8);
       const double per_step = tr.t_slice[wi][tr.ctas - 1] * dim / rows;
       const double cost = per_step * m;
       if (cost < best) {

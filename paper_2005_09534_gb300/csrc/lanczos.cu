@@ -228,9 +228,11 @@ int run_lanczos(polfed_ctx* c, HamPlan& plan, const LanczosParams& P, double* d_
   const int kind = P.o.precision == POLFED_F32 ? POLFED_F32 : (P.o.precision == POLFED_F64 ? POLFED_F64 : POLFED_DF64);
   if (P.N_ev < 1 || P.N_ev > dim) return fail(POLFED_EINVAL, "N_ev must be in 1..dim");
   int m_max = (int)std::ceil(P.o.cols_factor * (1.0 + P.o.k_margin) * P.N_ev / S) + 1;
-  // block Lanczos needs polynomial degree (steps) as well as columns: with few
-  // wanted pairs per block column the degree, not ms ~ 2 N_ev, limits convergence
-  m_max = std::max(m_max, 24);
+  // block Lanczos needs polynomial degree (steps) as well as columns: the
+  // accessible pairs start converging once ms ~ 2.2 (1 + k_margin) N_ev and
+  // then gain one to two digits per step, so allow 12 steps past that onset
+  const int onset = (int)std::ceil(2.2 * (1.0 + P.o.k_margin) * P.N_ev / S);
+  m_max = std::max(std::max(m_max, 24), onset + 12);
   m_max = (int)std::min<int64_t>(m_max, dim / S);
   if (m_max < 1) return fail(POLFED_EINVAL, "dimension too small for this block size");
   Dense& D = c->dense;
@@ -533,8 +535,10 @@ int extract(polfed_ctx* c, HamPlan& plan, const LanczosParams& P, const double* 
   const double p_rr = P.o.p - 0.02;
   std::vector<int> conv_idx;
   std::vector<char> used(n, 0);
+  // the FP32 stage (accept_any) hands every accessible Ritz vector to the
+  // refinement: subspace iteration needs the window's neighbours in the block
   for (int i = 0; i < n; i++)
-    if (theta[i] >= p_rr && tres[i] <= tol_sel) {
+    if (theta[i] >= p_rr && (tres[i] <= tol_sel || P.accept_any)) {
       conv_idx.push_back(i);
       used[i] = 1;
     }
@@ -1001,7 +1005,7 @@ int eigs_impl(polfed_ctx* c, const polfed_model* model, double eps_target, int32
   P.hook = hook;
   if (mixed) P.o.tol_conv = std::max(o.tol_conv, 2e-5);  // FP32 filter: stop at its noise floor
   LanczosOut lo;
-  int rc = POLFED_OK, restarts = 0;
+  int rc = POLFED_OK, restarts = 0, fallback = 0;
   for (;;) {
     LanczosOut cur;
     rc = run_lanczos(c, plan, P, d_evecs, cur);
@@ -1036,7 +1040,7 @@ int eigs_impl(polfed_ctx* c, const polfed_model* model, double eps_target, int32
     int Kr = std::max(16, K / 2);
     if (sigma == 0.0) Kr &= ~1;
     double mr_prev = 1e300;
-    for (int sweep = 0; sweep < 6; sweep++) {
+    for (int sweep = 0; sweep < 4; sweep++) {
       double mr = 0.0;
       for (double r : lo.resid_t) mr = std::max(mr, r);
       if (lo.n_out >= N_ev && mr <= P.tol_resid_t && sweep > 0) break;
@@ -1051,11 +1055,37 @@ int eigs_impl(polfed_ctx* c, const polfed_model* model, double eps_target, int32
       lo.n_refine++;
       lo.refine_K = Kr;
       Kr = std::min(2 * Kr, K);
+      if (sigma == 0.0) Kr &= ~1;
     }
     double mr = 0.0;
     for (double r : lo.resid_t) mr = std::max(mr, r);
     rc = (lo.n_out >= N_ev && mr <= P.tol_resid_t) ? POLFED_OK
                                                    : fail(POLFED_ENOCONV, "refinement did not reach the residual target");
+    if (rc != POLFED_OK) {
+      // The FP32 stage missed part of the wanted subspace (refinement cannot
+      // recover a direction the block does not contain): run the plain
+      // float-float method instead.
+      if (o.verbose || debug_on())
+        fprintf(stderr, "[polfed] refinement stalled at %.3e (H~): float-float POLFED run\n", mr);
+      LanczosParams P2 = P;
+      P2.o.precision = POLFED_DF64;
+      P2.o.tol_conv = o.tol_conv;
+      P2.accept_any = false;
+      LanczosOut l2;
+      rc = run_lanczos(c, plan, P2, d_evecs, l2);
+      if (rc != POLFED_OK && rc != POLFED_ENOCONV) return rc;
+      l2.matvec_cols += lo.matvec_cols;
+      l2.checks += lo.checks;
+      l2.t_filter += lo.t_filter;
+      l2.t_reorth += lo.t_reorth;
+      l2.t_qr += lo.t_qr;
+      l2.t_teig += lo.t_teig;
+      l2.t_ritz += lo.t_ritz;
+      l2.n_refine = lo.n_refine;
+      l2.refine_K = lo.refine_K;
+      lo = std::move(l2);
+      fallback = 1;
+    }
   }
   const double half = 0.5 * (e_hi - e_lo), mid = 0.5 * (e_hi + e_lo);
   const double hnorm = std::max(std::fabs(Emin), std::fabs(Emax));
@@ -1086,6 +1116,7 @@ int eigs_impl(polfed_ctx* c, const polfed_model* model, double eps_target, int32
   st.rho_sigma = rho_t;
   st.t_bounds = t_b;
   st.n_restarts = restarts;
+  st.fallback_df64 = fallback;
   st.dos_rule = o.dos_rule;
   st.bounds_from_hint = bounds_from_hint;
   st.t_filter = lo.t_filter;

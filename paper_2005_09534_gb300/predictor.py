@@ -51,7 +51,8 @@ def dataset(models, Ws, labels, augment=True):
 
 def fit(net: MLP, X: np.ndarray, Y: np.ndarray, steps=3000, lr=1e-3, batch=256, seed=0, device="cuda:0"):
     """Standardize with the training set's mean/std and run `steps` Adam steps on
-    random batches; returns (final full-set loss, seconds)."""
+    random batches, the learning rate decaying by a cosine from lr to lr/20;
+    returns (final full-set loss, seconds)."""
     import torch
     xm, xs = X.mean(axis=0), X.std(axis=0) + 1e-6
     ym, ys = Y.mean(axis=0), Y.std(axis=0) + 1e-6
@@ -65,11 +66,12 @@ def fit(net: MLP, X: np.ndarray, Y: np.ndarray, steps=3000, lr=1e-3, batch=256, 
     yb = torch.empty((b, Y.shape[1]), dtype=torch.float32, device=device)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(steps):
+    for k in range(steps):
         idx = torch.from_numpy(rng.integers(0, n, b)).to(device)
         torch.index_select(dX, 0, idx, out=xb)
         torch.index_select(dY, 0, idx, out=yb)
         torch.cuda.synchronize()
-        net.train_step(xb, yb, b, lr)
+        lr_k = lr * (0.05 + 0.95 * 0.5 * (1.0 + np.cos(np.pi * k / steps)))
+        net.train_step(xb, yb, b, float(lr_k))
     loss = net.grad(dX, dY, n)
     return loss, time.perf_counter() - t0

@@ -114,7 +114,8 @@ def test_eigs_batched_against_dense_ed(precision):
     evs, res, sts, status, info, rc = pf.eigs_batched(models, 0.5, nevs, n_b=0, opts=o, d_evecs=vecs,
                                                       allow_fail=True)
     diag = [(k, int(status[k]), sts[k]["n_b"], sts[k]["K"], sts[k]["m"], sts[k]["n_refine"], sts[k]["n_restarts"],
-             sts[k]["max_resid"] / refs[k]["norm"]) for k in range(len(spec))]
+             sts[k]["fallback_df64"], sts[k]["max_resid"] / refs[k]["norm"]) for k in range(len(spec))]
+    print("\nbatched", precision, diag)
     assert rc == 0 and list(status) == [0] * len(spec), diag
     assert info["rounds"] > 0 and info["workers"] == len(spec)
     assert info["n_width16"] + info["n_width32"] + info["n_width64"] == len(spec)

@@ -278,7 +278,7 @@ def test_trained_predictor_sets_K_better_than_the_gamma_rule():
         labels = predictor.labels_for(ctx, [m for m, _ in train])
     X, Y = predictor.dataset([m for m, _ in train], [W for _, W in train], labels)
     net = pf.MLP(L + 1, 128, 3, seed=3)
-    loss, secs = predictor.fit(net, X, Y, steps=3000, lr=1e-3, batch=256)
+    loss, secs = predictor.fit(net, X, Y, steps=6000, lr=2e-3, batch=256)
     rows = []
     for k, W in enumerate([1, 2, 3, 4, 6, 8] * 2):
         h = I.fields(L, W, 41, k)
