@@ -282,7 +282,8 @@ def main():
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": (tr or {}).get("dram_bytes_per_launch"),
             "peak_kind": f"of {peak_kind}", "kernel": "k_ham_step_tma (Clenshaw step on a 128-byte column slice)",
-            "alg_bytes_per_launch": alg_per_launch, "avg_launch_us": round(avg_launch * 1e6, 2)}
+            "alg_bytes_per_launch": alg_per_launch, "avg_launch_us": round(avg_launch * 1e6, 2),
+            "launches": int(agg["n_step_launches"]), "share_of_step": round(agg["step_gpu_s"] / max(t_dev, 1e-12), 4)}
     value = pairs_all / t_dev
     bytes_d2h = n_ev * dim * 8 + 2 * n_ev * 8
     line = {"metric": METRIC, "value": round(value, 4), "unit": "eigenpairs/s", "n_gpus": world,
