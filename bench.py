@@ -171,13 +171,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="L22_xxz_W3", choices=sorted(WORKLOADS) + sorted(BATCHED))
-    ap.add_argument("--precision", default="f32", choices=sorted(PREC))
+    ap.add_argument("--precision", default=None, choices=sorted(PREC),
+                    help="filter arithmetic (default: f32 stage + refinement; df64 for batched workloads)")
     ap.add_argument("--dos", default="mlp", choices=sorted(DOS),
                     help="density-of-states rule for K (mlp: the learned predictor, trained before timing)")
     ap.add_argument("--batch-mode", default="batched", choices=["batched", "sequential"],
                     help="batched workloads: one polfed_eigs_batched call, or polfed_eigs per realization")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
+    if args.precision is None:
+        args.precision = "df64" if args.workload in BATCHED else "f32"
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps; the number is not valid", file=sys.stderr)
     if args.impl == "reference":
@@ -263,6 +266,9 @@ def main():
         agg["status"].append(rc)
         agg["restarts"].append(st["n_restarts"])
         agg["refine"].append(st["n_refine"])
+        for key in ("t_bounds", "t_filter", "t_reorth", "t_qr", "t_teig", "t_ritz", "t_total"):
+            agg.setdefault(key, 0.0)
+            agg[key] += st[key]
         agg["max_rel_resid"] = max(agg["max_rel_resid"], rr)
     torch.cuda.synchronize()
     if dist:
@@ -294,7 +300,9 @@ def main():
                        "W": W, "N_ev": n_ev, "n_b": n_b, "eps": 0.5, "dos_rule": args.dos, "K": agg["K"],
                        "m": agg["m"], "restarts": agg["restarts"], "refine_sweeps": agg["refine"],
                        "parallelism": f"replicas x{world}", "l2": "per-step working set >> L2, no flush",
-                       "status": agg["status"], "max_resid_over_normH": agg["max_rel_resid"]},
+                       "status": agg["status"], "max_resid_over_normH": agg["max_rel_resid"],
+                       "phase_s": {k[2:]: round(agg[k], 2) for k in ("t_bounds", "t_filter", "t_reorth", "t_qr",
+                                                                       "t_teig", "t_ritz", "t_total") if k in agg}},
             "roofline": roof,
             "e2e": {"value": round(pairs_all / wall_s, 4), "unit": "eigenpairs/s",
                     "h2d_bytes_per_step": L * 8, "d2h_bytes_per_step": bytes_d2h},
