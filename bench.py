@@ -235,7 +235,7 @@ def main():
         return ok, st, rc, float(np.max(res) / hn)
 
     for w in range(args.warmup):
-        one(10_000 + w * world + rank, False)
+        one(warmup_realization(w, world, rank), False)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -251,7 +251,7 @@ def main():
     for k in range(args.steps):
         t0 = time.perf_counter()
         e0.record(stream)
-        ok, st, rc, rr = one(k * world + rank, True)
+        ok, st, rc, rr = one(timed_realization(k, world, rank), True)
         e1.record(stream)
         with torch.cuda.stream(stream):
             host_evecs.copy_(evecs, non_blocking=True)
@@ -316,6 +316,16 @@ def main():
     ctx.close()
     if dist:
         dist.destroy_process_group()
+
+
+def timed_realization(k, world, rank):
+    """Realization index of timed step k on this rank (ranks never share one)."""
+    return k * world + rank
+
+
+def warmup_realization(w, world, rank):
+    """Realization index of warm-up step w on this rank (disjoint from timed ones)."""
+    return 10_000 + w * world + rank
 
 
 def reduce_ranks(torch, dev, dist, t_dev, wall_s, pairs):
@@ -389,7 +399,7 @@ def run_batched(args, pf, torch, dev, world, rank, local, dist):
         return evs, res, sts, np.array(status), info, 0
 
     for w in range(args.warmup):
-        ms, nev = batched_models(spec, 10_000 + 1000 * (w * world + rank))
+        ms, nev = batched_models(spec, 1000 * warmup_realization(w, world, rank))
         solve(ms, nev)
     torch.cuda.synchronize()
     if dist:
@@ -400,7 +410,7 @@ def run_batched(args, pf, torch, dev, world, rank, local, dist):
     wall_s, dev_s, pairs = 0.0, 0.0, 0
     infos, statuses, max_rr, restarts, fallbacks = [], [], 0.0, 0, 0
     for k in range(args.steps):
-        ms, nev = batched_models(spec, 1000 * (k * world + rank))
+        ms, nev = batched_models(spec, 1000 * timed_realization(k, world, rank))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         evs, res, sts, status, info, rc = solve(ms, nev)
