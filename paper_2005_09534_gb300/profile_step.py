@@ -55,7 +55,7 @@ def main(argv):
     basis_build(L, L // 2, st)
     X = torch.from_numpy(I.block(dim, nb, 7)).to(dev, dt[1])
     Y = torch.empty_like(X)
-    bound = 1.5 * (L * 1.25 + L * 3.0 / 2)  # > ||H||: bonds (1/2 + 1/4) each, fields |h_i|/2 <= 3/2
+    bound = 1.5 * (L * 1.25 + L * 3.0 / 2)  # > ||H|| (each bond term <= 3/4, each field term <= 3/2)
     cheb_filter(m, st, dim, -bound, bound, 0.0, K, X, Y, nb, dt[0])
     torch.cuda.synchronize()
     print("profile_step ok", kind, L, dim, nb, K)
