@@ -558,10 +558,6 @@ int extract(polfed_ctx* c, HamPlan& plan, const LanczosParams& P, const double* 
   }
   const int nr = (int)conv_idx.size();
   const int npan = (nr + S - 1) / S;
-  // FP32 stage: the Rayleigh-Ritz step below runs on the whole Lanczos basis
-  // (its buffers are sized first so that the Ritz vectors formed here survive)
-  const int n_rr = P.accept_any ? m_done * S : nr;
-  PF_CHECK(ensure_ritz(c, dim, S, std::max(nr, n_rr), P.N_ev));
   // T eigenvectors are in c->evbuf (column-major n x n)
   double* Td = c->evbuf.as<double>();
   PF_CHECK(c->vecs.ensure(((size_t)n * npan * S + 64) * sizeof(double) + (size_t)npan * S * sizeof(int), &c->ws_total,
@@ -572,15 +568,10 @@ int extract(polfed_ctx* c, HamPlan& plan, const LanczosParams& P, const double* 
   k_gather_cols<<<1024, 256, 0, s>>>(Td, n, idx_d, nr, n, Vsel, n);
   PF_CUDA(cudaGetLastError());
   count_launch();
+  PF_CHECK(ensure_ritz(c, dim, S, nr, P.N_ev));
   double* Ur = c->ritz.as<double>();  // npan panels
   PF_CHECK(D.update(Qb, pstride, m_done, Vsel, 1, n, nr, Ur, pstride, 1.0, 0.0, s));
   out.ritz_cols = nr;
-  // FP32 stage: Rayleigh-Ritz with the FP64 H~ on span(Q_1..Q_m) itself.  The
-  // basis is exactly orthonormal in FP64 and holds the wanted eigenvectors far
-  // more accurately than the FP32-filtered Ritz vectors do; if its pairs pass
-  // the residual check no refinement sweep is needed.  The accessible Ritz
-  // vectors formed above stay in the buffer as the sweeps' input.
-  if (P.accept_any) return rr_select(c, plan, P, Qb, n_rr, d_evecs, out);
   return rr_select(c, plan, P, Ur, nr, d_evecs, out);
 }
 
@@ -1052,7 +1043,7 @@ int eigs_impl(polfed_ctx* c, const polfed_model* model, double eps_target, int32
     for (int sweep = 0; sweep < 4; sweep++) {
       double mr = 0.0;
       for (double r : lo.resid_t) mr = std::max(mr, r);
-      if (lo.n_out >= N_ev && mr <= P.tol_resid_t) break;
+      if (lo.n_out >= N_ev && mr <= P.tol_resid_t && sweep > 0) break;
       if (sweep >= 3 && mr > 0.5 * mr_prev) break;  // stagnating: more sweeps will not help
       mr_prev = mr;
       if (o.verbose || debug_on())

@@ -94,15 +94,14 @@ def test_block_lanczos_with_given_bounds():
 
 
 def test_mixed_precision_f32_stage_with_refinement():
-    """FP32 filter for the Lanczos stage, then Rayleigh-Ritz with the FP64 H~
-    on the whole Lanczos basis and, where that falls short, float-float
-    Jackson-filter + FP64 Rayleigh-Ritz sweeps: same bar as the FP64-class paths."""
+    """FP32 filter for the Lanczos stage, then float-float Jackson-filter +
+    FP64 Rayleigh-Ritz refinement sweeps: same bar as the FP64-class paths."""
     torch, dev = torch_dev()
     pf = lib()
     m = I.xxz(14, 3.0, 1, 0)
     r = O.eigs_nearest(m.L, m.J1, m.J2, m.Delta, m.h, True, 0.5, 50)
     ev, res, st, V = _run(pf, torch, dev, m, 0.5, 50, 16, pf.F32)
-    assert st["fallback_df64"] == 0  # the FP32-stage result itself was brought to the bar
+    assert st["n_refine"] >= 1
     # eigenvalues, residuals, overlap and gap ratio at the full bar; the
     # entropy follows the eigenvector error (~ residual / level spacing) at
     # first order, which the residual target of 1e-8 ||H|| leaves near 1e-7
