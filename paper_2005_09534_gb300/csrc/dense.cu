@@ -6,6 +6,7 @@
 // Panels are row-major N x S (ld = S) and a basis is panel-major (panel j at j * N * S).
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 #include "dense.h"
 
@@ -415,9 +416,11 @@ void Dense::release() {
 
 int Dense::configure() {
   // allow the large dynamic shared memory of the S = 128 kernels
+  static std::mutex mu;  // worker threads of the batched runner configure concurrently
   static bool done[64] = {false};
   int dev = 0;
   cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
   if (dev < 64 && done[dev]) return POLFED_OK;
   const int big = 200 * 1024;
   PF_CUDA(cudaFuncSetAttribute(k_update<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));

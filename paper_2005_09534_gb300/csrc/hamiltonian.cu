@@ -1443,6 +1443,21 @@ static bool pow2_or_zero(double v) {
   return m == 0.5 && e > -120 && e < 120;
 }
 
+// Per-kernel, per-device launch configuration (shared-memory limit, SM count,
+// occupancy), filled once under its mutex.
+struct LaunchCache {
+  static constexpr int kDevices = 64;
+  struct Dev {
+    bool set = false;
+    int nsm = 0;
+    size_t maxdyn = 0;
+    size_t occ_smem = 0;
+    int occ = 0;
+  };
+  std::mutex mu;
+  Dev d[kDevices];
+};
+
 template <class NT, int LPR, bool J2>
 static int launch_step_t(const HamPlan& p, const StepArgs& a, cudaStream_t s) {
   if (p.geo.n_cross > (J2 ? 6 : 2)) return fail(POLFED_EINVAL, "more cross bonds than the kernel handles");
@@ -1452,36 +1467,35 @@ static int launch_step_t(const HamPlan& p, const StepArgs& a, cudaStream_t s) {
   const HamGeometry& g = p.geo;
   const size_t smem = (size_t)g.max_group * W * sizeof(S) + (((size_t)1 << g.b) + ((size_t)1 << g.n_cross)) * sizeof(C);
   auto kern = k_ham_step<NT, LPR, J2>;
-  static int configured_dev[64] = {0};
-  static size_t configured_smem[64] = {0};
+  // per-device launch configuration of this kernel, computed once under a
+  // mutex (the batched runner's worker threads launch concurrently)
+  static LaunchCache cache;
   int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 64 && !configured_dev[dev]) {
-    int optin = 0;
-    PF_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    cudaFuncAttributes fa;
-    PF_CUDA(cudaFuncGetAttributes(&fa, kern));
-    const int maxdyn = optin - (int)fa.sharedSizeBytes;
-    PF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, maxdyn));
-    configured_dev[dev] = 1;
-    configured_smem[dev] = (size_t)maxdyn;
-  }
-  if (dev < 64 && smem > configured_smem[dev]) return fail(POLFED_EINVAL, "slice tile does not fit in shared memory");
-  static int nsm_cache[64] = {0};
-  static size_t occ_smem[64] = {0};
-  static int occ_cache[64] = {0};
-  if (dev < 64 && !nsm_cache[dev]) cudaDeviceGetAttribute(&nsm_cache[dev], cudaDevAttrMultiProcessorCount, dev);
-  const int nsm = dev < 64 ? nsm_cache[dev] : 152;
+  PF_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= LaunchCache::kDevices) return fail(POLFED_EINVAL, "device ordinal beyond the launch cache");
   const int threads = 256;
-  int occ = 1;
-  if (dev < 64 && occ_smem[dev] == smem && occ_cache[dev] > 0) {
-    occ = occ_cache[dev];
-  } else {
-    PF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem));
-    if (dev < 64) {
-      occ_smem[dev] = smem;
-      occ_cache[dev] = occ;
+  int nsm = 0, occ = 0;
+  {
+    std::lock_guard<std::mutex> lk(cache.mu);
+    LaunchCache::Dev& c = cache.d[dev];
+    if (!c.set) {
+      int optin = 0;
+      PF_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+      cudaFuncAttributes fa;
+      PF_CUDA(cudaFuncGetAttributes(&fa, kern));
+      const int maxdyn = optin - (int)fa.sharedSizeBytes;
+      PF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, maxdyn));
+      PF_CUDA(cudaDeviceGetAttribute(&c.nsm, cudaDevAttrMultiProcessorCount, dev));
+      c.maxdyn = (size_t)maxdyn;
+      c.set = true;
     }
+    if (smem > c.maxdyn) return fail(POLFED_EINVAL, "slice tile does not fit in shared memory");
+    if (c.occ_smem != smem || c.occ <= 0) {
+      PF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ, kern, threads, smem));
+      c.occ_smem = smem;
+    }
+    nsm = c.nsm;
+    occ = c.occ;
   }
   if (occ < 1) return fail(POLFED_EINVAL, "step kernel cannot be resident (shared memory)");
   int grid = std::min(g.n_groups, nsm * occ);
@@ -1527,12 +1541,11 @@ static size_t tma_smem_bytes(const HamGeometry& g, size_t esz_c, bool j2) {
 }
 
 static bool tma_disabled() {
-  static int v = -1;
-  if (v < 0) {
+  static const bool v = [] {
     const char* e = getenv("POLFED_NO_TMA");
-    v = (e && e[0] == '1') ? 1 : 0;
-  }
-  return v == 1;
+    return e && e[0] == '1';
+  }();
+  return v;
 }
 
 template <class NT, bool J2>
@@ -1542,20 +1555,25 @@ static int launch_step_tma(const HamPlan& p, const StepArgs& a, cudaStream_t s) 
   const HamGeometry& g = p.geo;
   const size_t smem = tma_smem_bytes(g, sizeof(C), J2);
   auto kern = k_ham_step_tma<NT, J2>;
-  static int configured[64] = {0};
-  static int nsm_cache[64] = {0};
+  static LaunchCache cache;  // see launch_step_t
   int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 64 && !configured[dev]) {
-    int optin = 0;
-    PF_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    cudaFuncAttributes fa;
-    PF_CUDA(cudaFuncGetAttributes(&fa, kern));
-    PF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes));
-    cudaDeviceGetAttribute(&nsm_cache[dev], cudaDevAttrMultiProcessorCount, dev);
-    configured[dev] = 1;
+  PF_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= LaunchCache::kDevices) return fail(POLFED_EINVAL, "device ordinal beyond the launch cache");
+  int nsm = 0;
+  {
+    std::lock_guard<std::mutex> lk(cache.mu);
+    LaunchCache::Dev& c = cache.d[dev];
+    if (!c.set) {
+      int optin = 0;
+      PF_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+      cudaFuncAttributes fa;
+      PF_CUDA(cudaFuncGetAttributes(&fa, kern));
+      PF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes));
+      PF_CUDA(cudaDeviceGetAttribute(&c.nsm, cudaDevAttrMultiProcessorCount, dev));
+      c.set = true;
+    }
+    nsm = c.nsm;
   }
-  const int nsm = dev < 64 ? nsm_cache[dev] : 152;
   const int grid = std::min(g.n_groups, nsm);
   const int kk = std::is_same<NT, NF32>::value ? POLFED_F32 : (std::is_same<NT, NF64>::value ? POLFED_F64 : POLFED_DF64);
   StepTables t{p.tab.rec, p.tab.grec, nullptr, nullptr, nullptr, p.tab.order};

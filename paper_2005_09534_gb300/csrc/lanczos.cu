@@ -31,12 +31,11 @@ using namespace polfed;
 namespace {
 
 bool debug_on() {
-  static int v = -1;
-  if (v < 0) {
+  static const bool v = [] {
     const char* e = getenv("POLFED_DEBUG");
-    v = (e && e[0] == '1') ? 1 : 0;
-  }
-  return v == 1;
+    return e && e[0] == '1';
+  }();
+  return v;
 }
 
 double now_s() {
