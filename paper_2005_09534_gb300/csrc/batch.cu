@@ -380,6 +380,7 @@ int polfed_eigs_batched(int32_t device, int32_t n_inst, const polfed_model* mode
   for (int i = 0; i < n_inst; i++) {
     if (nev[i] < 1) return fail(POLFED_EINVAL, "N_ev must be >= 1");
     off[i + 1] = off[i] + nev[i];
+    status[i] = POLFED_ECUDA;  // until a worker has run the realization
   }
   // 1. autotuning of the block widths and the grid
   TuneResult tr;
