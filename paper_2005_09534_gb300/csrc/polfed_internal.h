@@ -98,7 +98,7 @@ struct HamTables {
   struct GroupRec* grec;
 };
 
-constexpr int kMaxHigh = 24;
+constexpr int kMaxHigh = 32;  // high bonds: L = 24 J1-J2 with b = 10 has 13 + 12 = 25
 // Per-group constants (one group = rows sharing s_hi), precomputed per plan.
 struct alignas(16) GroupRec {
   int r0, n_g, cls_base, n_hn1, n_hn, need_mask, pad0, pad1;

@@ -142,3 +142,29 @@ def test_eigs_batched_matches_separate_runs_and_fixed_width():
             ev, r, st, rc1 = pf.eigs(ctx, m, 0.5, 30, 0, 32, o)
             nrm = max(abs(st["E_min"]), abs(st["E_max"]))
             assert np.max(np.abs(ev - evs[k])) <= 1e-10 * nrm
+
+
+def test_filter_batched_full_size_matches_single_filters():
+    """Realizations of the batched workload's sizes (L = 16 and 18, dim 12870 and
+    48620): one batched launch equals separate polfed_cheb_filter calls."""
+    torch, dev = torch_dev()
+    pf = lib()
+    spec = [(16, 2.0, 300), (18, 6.0, 120), (16, 8.0, 37), (18, 1.0, 500)]
+    ms, Xs, Ys, Ks, lo, hi = [], [], [], [], [], []
+    for k, (L, W, K) in enumerate(spec):
+        m = I.xxz(L, W, 25, k)
+        dim, st = device_basis(pf, torch, dev, L)
+        bound = L * 0.75 + 0.5 * float(np.abs(m.h).sum()) + 0.1  # > ||H||
+        ms.append(m)
+        Ks.append(K)
+        lo.append(-bound)
+        hi.append(bound)
+        Xs.append(torch.from_numpy(I.block(dim, 16, 900 + k)).to(dev))
+        Ys.append(torch.empty_like(Xs[-1]))
+    pf.cheb_filter_batched(ms, lo, hi, [0.0] * 4, Ks, Xs, Ys, 16, pf.DF64)
+    for k, m in enumerate(ms):
+        dim, st = device_basis(pf, torch, dev, m.L)
+        Y1 = torch.empty_like(Xs[k])
+        pf.cheb_filter(m, st, dim, lo[k], hi[k], 0.0, Ks[k], Xs[k], Y1, 16, pf.DF64)
+        err = torch.max(torch.abs(Ys[k] - Y1)).item() / torch.max(torch.abs(Xs[k])).item()
+        assert err < 1e-12 * (Ks[k] + 1), (k, err)

@@ -69,7 +69,7 @@ def test_h_apply_vs_dense(L, n_b):
                 assert err < _tol(dtype) * (10 if dtype == pf.F32 else 1) * max(1, L / 4), (mi, lo, dtype, err)
 
 
-@pytest.mark.parametrize("L,n_b", [(20, 32), (22, 64)])
+@pytest.mark.parametrize("L,n_b", [(20, 32), (22, 64), (24, 64)])
 def test_h_apply_full_size_sampled_rows(L, n_b):
     torch, dev = torch_dev()
     pf = lib()
