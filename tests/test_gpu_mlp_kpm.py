@@ -230,7 +230,7 @@ def test_eigs_under_each_dos_rule(rule):
     assert np.max(res) <= 1e-8 * nrm
 
 
-def test_bounds_hints_are_judged_by_the_probe():
+def test_bounds_hints_are_checked_by_the_probe():
     torch, dev = torch_dev()
     pf = lib()
     m = I.xxz(14, 3.0, 1, 2)
