@@ -115,13 +115,16 @@ typedef struct polfed_stats {
   double max_resid;      /* max ||H u - E u|| over the returned pairs (H units) */
   double t_bounds, t_filter, t_reorth, t_qr, t_teig, t_ritz, t_total; /* seconds */
   int64_t n_launches;      /* kernels this library launched during the call */
-  int64_t n_step_launches; /* launches of the Chebyshev / H~ step kernel */
+  int64_t n_step_launches; /* launches of the Chebyshev step kernels inside event-timed filter runs */
   double step_gpu_s;       /* device time of those launches (CUDA events on the launching stream) */
   double step_alg_bytes;   /* algorithmic bytes of those launches: N * cols * w * (3 + [c_k != 0]) each */
   int32_t dos_rule;        /* rule that set K */
   int32_t bounds_from_hint;/* 1 if [e_lo, e_hi] came from the caller's (probe-confirmed) bounds hints */
   int32_t n_restarts;      /* restarts with a smaller K because fewer than N_ev eigenvalues had P >= p */
   int32_t fallback_df64;   /* POLFED_F32: 1 if the refinement stalled and a float-float run replaced it */
+  int64_t kind_launches[3];  /* the three step counters above by storage kind, */
+  double kind_gpu_s[3];      /* indexed POLFED_F64, POLFED_F32, POLFED_DF64 */
+  double kind_alg_bytes[3];
 } polfed_stats;
 
 typedef struct polfed_ctx polfed_ctx;

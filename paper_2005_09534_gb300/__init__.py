@@ -68,10 +68,15 @@ class CStats(ctypes.Structure):
                 ("t_teig", c_double), ("t_ritz", c_double), ("t_total", c_double),
                 ("n_launches", c_int64), ("n_step_launches", c_int64), ("step_gpu_s", c_double),
                 ("step_alg_bytes", c_double), ("dos_rule", c_int32), ("bounds_from_hint", c_int32),
-                ("n_restarts", c_int32), ("fallback_df64", c_int32)]
+                ("n_restarts", c_int32), ("fallback_df64", c_int32), ("kind_launches", c_int64 * 3),
+                ("kind_gpu_s", c_double * 3), ("kind_alg_bytes", c_double * 3)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_}
+        d = {}
+        for f, _ in self._fields_:
+            v = getattr(self, f)
+            d[f] = list(v) if f.startswith("kind_") else v
+        return d
 
 
 class CBatchInfo(ctypes.Structure):

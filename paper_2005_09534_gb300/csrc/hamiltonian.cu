@@ -1527,10 +1527,7 @@ static int launch_step_t(const HamPlan& p, const StepArgs& a, cudaStream_t s) {
   kern<<<grid, threads, smem, s>>>(g, t, (const S*)a.b1, (const S*)a.b2, (const S*)a.x, (S*)a.out, kc,
                                    a.cX != 0.0 && a.x != nullptr, a.cB != 0.0 && a.b2 != nullptr);
   PF_CUDA(cudaGetLastError());
-  Counters& cn = counters();
-  cn.launches++;
-  cn.step_launches++;
-  cn.step_alg_bytes += (double)g.dim * W * sizeof(S) * (3.0 + (a.cX != 0.0 ? 1.0 : 0.0));
+  count_step(kk, (double)g.dim * W * sizeof(S) * (3.0 + (a.cX != 0.0 ? 1.0 : 0.0)));
   return POLFED_OK;
 }
 
@@ -1603,10 +1600,7 @@ static int launch_step_tma(const HamPlan& p, const StepArgs& a, cudaStream_t s) 
   kern<<<grid, kTmaThreads, smem, s>>>(g, t, (const S*)a.b1, (const S*)a.b2, (const S*)a.x, (S*)a.out, kc,
                                        a.cX != 0.0 && a.x != nullptr, a.cB != 0.0 && a.b2 != nullptr, p.err_flag);
   PF_CUDA(cudaGetLastError());
-  Counters& cn = counters();
-  cn.launches++;
-  cn.step_launches++;
-  cn.step_alg_bytes += (double)g.dim * 128.0 * (3.0 + (a.cX != 0.0 ? 1.0 : 0.0));
+  count_step(kk, (double)g.dim * 128.0 * (3.0 + (a.cX != 0.0 ? 1.0 : 0.0)));
   return POLFED_OK;
 }
 
@@ -1724,10 +1718,17 @@ static int slice_out(int kind, int abi_kind, const void* ys, int64_t dim, int W,
 }
 
 // Device time of a run of step launches, by a pair of CUDA events on the launching stream.
+// The launches of storage kind `kind` issued between construction and stop()
+// are credited to the timed counters with the measured time.
 struct StepTimer {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaStream_t s;
-  explicit StepTimer(cudaStream_t st) : s(st) {
+  int kind;
+  int64_t n0;
+  double b0;
+  StepTimer(cudaStream_t st, int k) : s(st), kind(k) {
+    n0 = counters().all_launches[kind];
+    b0 = counters().all_alg_bytes[kind];
     if (cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) cudaEventRecord(e0, s);
   }
   int stop() {
@@ -1736,7 +1737,15 @@ struct StepTimer {
     PF_CUDA(cudaEventSynchronize(e1));
     float ms = 0.f;
     PF_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-    counters().step_gpu_s += 1e-3 * ms;
+    Counters& c = counters();
+    const int64_t n = c.all_launches[kind] - n0;
+    const double b = c.all_alg_bytes[kind] - b0;
+    c.step_gpu_s += 1e-3 * ms;
+    c.step_launches += n;
+    c.step_alg_bytes += b;
+    c.kind_gpu_s[kind] += 1e-3 * ms;
+    c.kind_launches[kind] += n;
+    c.kind_alg_bytes[kind] += b;
     return POLFED_OK;
   }
   ~StepTimer() {
@@ -1777,7 +1786,7 @@ int filter_block(HamPlan& plan, int kind, const double* c, int K, double invD, c
     PF_CHECK(slice_in(kind, abi_kind, in, dim, n_b, col0, ncols, W, scr.xs, scr.ba, scr.bb, c[K], scr.flag, s));
     void* cur = scr.ba;  // b_{k+1}
     void* oth = scr.bb;  // b_{k+2}, overwritten in place by b_k
-    StepTimer tm(s);
+    StepTimer tm(s, kind);
     for (int k = K - 1; k >= 1; k--) {
       StepArgs a{cur, oth, scr.xs, oth, c[k], 2.0, (k == K - 1) ? 0.0 : -1.0, lpr};
       PF_CHECK(launch_ham_step(plan, kind, a, s));
@@ -1873,7 +1882,6 @@ int launch_batched(const BatchJob* d_jobs, int n_jobs, int n_steps, int tile_ele
   void* args[] = {(void*)&d_jobs, (void*)&n_jobs, (void*)&n_steps, (void*)&tile_elems, (void*)&nlo_max,
                   (void*)&count, (void*)&gen, (void*)&err};
   PF_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(256), args, smem, s));
-  count_launch();
   *grid_out = grid;
   return POLFED_OK;
 }
@@ -1965,7 +1973,7 @@ int filter_batched(std::vector<BatchFilterItem>& items, int kind, int abi_kind, 
     unsigned* bar = (unsigned*)(base + Lo.bar_off);
     int* err = (int*)(bar + 2);
     int grid = 0;
-    StepTimer tm(s);
+    StepTimer tm(s, kind);
     int rc;
     if (kind == POLFED_F32)
       rc = j2 ? launch_batched<NF32, true>((const BatchJob*)base, (int)jobs.size(), n_steps, tile_elems, nlo_max, bar,
@@ -1978,11 +1986,10 @@ int filter_batched(std::vector<BatchFilterItem>& items, int kind, int abi_kind, 
               : launch_batched<NDF, false>((const BatchJob*)base, (int)jobs.size(), n_steps, tile_elems, nlo_max, bar,
                                            err, ctas_per_sm, s, &grid);
     if (rc != POLFED_OK) return rc;
+    count_step(kind, alg);  // one launch carrying every job's steps
     const double g0 = counters().step_gpu_s;
     PF_CHECK(tm.stop());
     Counters& cn = counters();
-    cn.step_launches++;
-    cn.step_alg_bytes += alg;
     if (bst) {
       bst->n_jobs = (int)jobs.size();
       bst->n_steps = n_steps;

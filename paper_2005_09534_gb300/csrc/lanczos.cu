@@ -1129,6 +1129,11 @@ int eigs_impl(polfed_ctx* c, const polfed_model* model, double eps_target, int32
   st.n_step_launches = cn1.step_launches - cn0.step_launches;
   st.step_gpu_s = cn1.step_gpu_s - cn0.step_gpu_s;
   st.step_alg_bytes = cn1.step_alg_bytes - cn0.step_alg_bytes;
+  for (int k = 0; k < 3; k++) {
+    st.kind_launches[k] = cn1.kind_launches[k] - cn0.kind_launches[k];
+    st.kind_gpu_s[k] = cn1.kind_gpu_s[k] - cn0.kind_gpu_s[k];
+    st.kind_alg_bytes[k] = cn1.kind_alg_bytes[k] - cn0.kind_alg_bytes[k];
+  }
   c->last = st;
   if (stats) *stats = st;
   if (rc == POLFED_OK && st.max_resid > o.tol_resid * hnorm && o.verbose)

@@ -37,12 +37,27 @@ int fail(int code, const std::string& msg);  // set_error + return code
 // time (CUDA events on the launching stream); calls report their deltas.
 struct Counters {
   int64_t launches = 0;
+  // step-kernel launches inside CUDA-event-timed runs (see StepTimer), in all
+  // and by storage kind (index POLFED_F64 / POLFED_F32 / POLFED_DF64)
   int64_t step_launches = 0;
   double step_gpu_s = 0.0;
   double step_alg_bytes = 0.0;
+  int64_t kind_launches[3] = {0, 0, 0};
+  double kind_gpu_s[3] = {0.0, 0.0, 0.0};
+  double kind_alg_bytes[3] = {0.0, 0.0, 0.0};
+  // every step-kernel launch, timed or not (the timer reads its share from these)
+  int64_t all_launches[3] = {0, 0, 0};
+  double all_alg_bytes[3] = {0.0, 0.0, 0.0};
 };
 Counters& counters();
 inline void count_launch(int64_t n = 1) { counters().launches += n; }
+// count one step-kernel launch of storage kind `kind` moving `alg_bytes` algorithmic bytes
+inline void count_step(int kind, double alg_bytes) {
+  Counters& c = counters();
+  c.launches++;
+  c.all_launches[kind]++;
+  c.all_alg_bytes[kind] += alg_bytes;
+}
 
 // -------------------------------------------------------------- binomials
 // C(n, k) for 0 <= n, k <= 32 (C(32,16) < 2^31).
