@@ -120,7 +120,14 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def oracle_sample(seconds=12.0):
+# Chebyshev block steps (K x m) of the float32 stage for each single workload, as measured by
+# polfed_eigs on GB300 (method parameters: they follow from the density of states and N_ev,
+# not from the hardware).  The CPU estimates below multiply the oracle's time per step by them.
+KM_STEPS = {"L22_xxz_W3": (9472, 23), "L20_j1j2_W4": (5958, 20), "L14_xxz_W3": (352, 14),
+            "L24_j1j2_W5": (20000, 44)}
+
+
+def oracle_dense_sample(seconds=12.0):
     """The CPU oracle (dense ED of the S^z=0 block, LAPACK eigh) on L=14 XXZ chains,
     N_ev=50 nearest eps=0.5, repeated over realizations for about `seconds`."""
     import oracle as O
@@ -136,30 +143,72 @@ def oracle_sample(seconds=12.0):
     dt = time.perf_counter() - t0
     return {"value": n_pairs / dt, "unit": "eigenpairs/s", "cores": os.cpu_count(), "kind": "oracle",
             "sample": f"dense ED (numpy eigh, default BLAS threads) of {n_real} L=14 XXZ W=3 realizations, "
-                      f"N_ev=50 each, {dt:.1f} s; dense ED at L=22 (705432^2 FP64, 4 TB) is infeasible"}
+                      f"N_ev=50 each, {dt:.1f} s"}
+
+
+def oracle_filter_sample(workload, K_run=None, m_run=None, seconds=12.0, realization=0):
+    """A bounded sample of the workload itself on the host: the oracle's filter by the
+    matrix three-term recurrence (filter_matrix_powers) on the workload's sparse H~
+    (scipy CSR, single-threaded SpMM) for the workload's n_b columns, run for about
+    `seconds`; the rate is extrapolated to a whole run by its K x m block steps of the
+    float32 stage (refinement and FP64 work left out, so the CPU time is a lower bound)."""
+    import scipy.sparse as sp
+    import oracle as O
+    builder, L, W, n_ev, n_b, cfg = WORKLOADS[workload]
+    K, m = (K_run, m_run) if K_run else KM_STEPS[workload]
+    md = builder(L, W, cfg, realization)
+    t_b0 = time.perf_counter()
+    H, _ = O.sparse_hamiltonian(md.L, md.J1, md.J2, md.Delta, md.h, md.periodic)
+    t_build = time.perf_counter() - t_b0
+    nb1 = L if md.periodic else L - 1
+    nb2 = L if md.periodic else L - 2
+    bound = (nb1 * abs(md.J1) + nb2 * abs(md.J2)) * (0.5 + abs(md.Delta) / 4) + 0.5 * float(np.abs(md.h).sum())
+    Ht = (H / bound).tocsr()  # H~ for [e_lo, e_hi] = [-bound, bound] (bound >= ||H||)
+    X = I.block(H.shape[0], n_b, 11)
+    c, D = O.cheb_coeffs(0.0, 4)
+    O.filter_matrix_powers(Ht, X, c, D)  # warm-up
+    steps, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        O.filter_matrix_powers(Ht, X, c, D)
+        steps += 4
+    t_step = (time.perf_counter() - t0) / steps
+    t_run = K * m * t_step
+    return {"value": n_ev / t_run, "unit": "eigenpairs/s", "cores": 1, "kind": "oracle",
+            "sample": f"oracle filter_matrix_powers on the {workload} sparse H~ (dim {H.shape[0]}, {n_b} columns, "
+                      f"scipy CSR SpMM, 1 thread): {steps} Chebyshev steps in {steps * t_step:.1f} s "
+                      f"({t_step:.3f} s/step, H built in {t_build:.1f} s), extrapolated to the run's "
+                      f"K x m = {K} x {m} block steps of the float32 stage (a lower bound on the CPU time: "
+                      f"refinement and FP64 work left out)",
+            "seconds_per_step": t_step, "extrapolated_run_s": t_run}
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    if args.workload in BATCHED:
+        sample = lambda secs: oracle_dense_sample(secs)
+        cfg = {"workload": "L14_xxz_W3 dense-ED sample (bounded stand-in for " + args.workload + ")",
+               "N_ev": 50, "eps": 0.5}
+    else:
+        sample = lambda secs: oracle_filter_sample(args.workload, seconds=secs)
+        builder, L, W, n_ev, n_b, c_id = WORKLOADS[args.workload]
+        cfg = {"workload": args.workload, "L": L, "W": W, "N_ev": n_ev, "n_b": n_b, "eps": 0.5,
+               "estimate": "oracle filter rate extrapolated by K x m block steps"}
     for _ in range(args.warmup):
-        oracle_sample(0.0)
-    vals = []
-    t_all = 0.0
+        sample(1.0)
+    vals, last = [], None
     for _ in range(args.steps):
-        s = oracle_sample(3.0)
-        vals.append(s["value"])
-        t_all += 50.0 / s["value"]
+        last = sample(8.0)
+        vals.append(last["value"])
     value = float(np.mean(vals))
-    cb = oracle_sample(3.0)
+    cb = dict(last)
     cb["value"] = value
+    n_ev = cfg["N_ev"]
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "eigenpairs/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * 50.0 / value,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * n_ev / value,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "L14_xxz_W3 dense-ED sample (bounded stand-in for " + args.workload + ")",
-                       "N_ev": 50, "eps": 0.5},
-            "cpu_baseline": cb,
+            "config": cfg, "cpu_baseline": cb,
             "e2e": {"value": value, "unit": "eigenpairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -324,7 +373,10 @@ def main():
     if mlp_info:
         line["config"]["mlp"] = mlp_info
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = oracle_sample()
+        line["cpu_baseline"] = oracle_filter_sample(args.workload, K_run=int(np.mean(agg["K"])),
+                                                    m_run=int(round(np.mean(agg["m"]))))
+        if L > 14:
+            line["cpu_dense_ed_L14"] = oracle_dense_sample(8.0)
     print(json.dumps(line), flush=True)
     ctx.close()
     if dist:
