@@ -36,7 +36,9 @@ WORKLOADS = {
     "L24_j1j2_W5": (I.j1j2, 24, 5.0, 1000, 64, 5),
 }
 # 64 XXZ rings, L = 16 / 18 alternating, W cycling {1,2,3,4,6,8}, N_ev cycling {50,100,200}
-BATCHED = {"batched64_L16_L18": (64, (16, 18), (1.0, 2.0, 3.0, 4.0, 6.0, 8.0), (50, 100, 200), 3)}
+BATCHED = {"batched64_L16_L18": (64, (16, 18), (1.0, 2.0, 3.0, 4.0, 6.0, 8.0), (50, 100, 200), 3),
+           # a small batch of the same kind for quick checks
+           "batched8_L12_L14": (8, (12, 14), (1.0, 3.0, 6.0, 8.0), (20, 40), 3)}
 PREC = {"df64": 2, "f64": 0, "f32": 1}
 DOS = {"moments": 0, "gamma": 1, "kpm": 2, "mlp": 3}
 
@@ -180,6 +182,33 @@ def oracle_filter_sample(workload, K_run=None, m_run=None, seconds=12.0, realiza
                       f"K x m = {K} x {m} block steps of the float32 stage (a lower bound on the CPU time: "
                       f"refinement and FP64 work left out)",
             "seconds_per_step": t_step, "extrapolated_run_s": t_run}
+
+
+def oracle_batched_sample(ms, nev, sts, seconds=5.0):
+    """The batched workload on the host: the oracle's filter rate per Chebyshev step for one
+    realization of each chain length (n_b = 16), extrapolated by every realization's own
+    K x m x (n_b / 16) block steps from the GPU run (a lower bound, as in oracle_filter_sample)."""
+    import oracle as O
+    rate = {}
+    for md in ms:
+        if md.L in rate:
+            continue
+        H, _ = O.sparse_hamiltonian(md.L, md.J1, md.J2, md.Delta, md.h, md.periodic)
+        bound = 2 * md.L * (0.5 + abs(md.Delta) / 4) + 0.5 * float(np.abs(md.h).sum())
+        Ht = (H / bound).tocsr()
+        X = I.block(H.shape[0], 16, 12)
+        c, D = O.cheb_coeffs(0.0, 4)
+        steps, t0 = 0, time.perf_counter()
+        while time.perf_counter() - t0 < seconds:
+            O.filter_matrix_powers(Ht, X, c, D)
+            steps += 4
+        rate[md.L] = (time.perf_counter() - t0) / steps
+    t_run = sum(st["K"] * st["m"] * max(1, st["n_b"] // 16) * rate[md.L] for md, st in zip(ms, sts))
+    return {"value": sum(nev) / t_run, "unit": "eigenpairs/s", "cores": 1, "kind": "oracle",
+            "sample": "oracle filter_matrix_powers on one sparse H~ per chain length (16 columns, scipy CSR, "
+                      "1 thread): " + ", ".join(f"L={L}: {t:.4f} s/step" for L, t in sorted(rate.items()))
+                      + f"; extrapolated by each realization's K x m block steps: {t_run:.0f} s for the batch "
+                        "(a lower bound: refinement and FP64 work left out)"}
 
 
 def run_reference(args):
@@ -535,6 +564,8 @@ def run_batched(args, pf, torch, dev, world, rank, local, dist):
                     "d2h_bytes_per_step": 16 * sum(batched_models(spec, 0)[1])},
             "gpu_launches": int(sum(i["n_launches"] for i in infos)),
             "clocks": ck}
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_batched_sample(ms, nev, sts)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
