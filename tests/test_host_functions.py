@@ -59,3 +59,17 @@ def test_symmetry_copies_share_the_spectrum():
         for c in copies:
             ev = np.linalg.eigvalsh(O.dense_hamiltonian(L, 1.0, J2, 0.55, c, periodic)[0])
             assert np.max(np.abs(ev - ref)) < 1e-11
+
+
+def test_predictor_dataset_rows(pf):
+    """dataset() stacks one feature/target row per symmetry copy, with the shared labels."""
+    from paper_2005_09534_gb300 import predictor
+    ms = [I.xxz(10, 2.0, 33, 0), I.xxz(10, 5.0, 33, 1)]
+    labels = np.array([[-9.0, 7.0, 1.1], [-12.0, 10.0, 0.9]])
+    X, Y = predictor.dataset(ms, [2.0, 5.0], labels)
+    assert X.shape == (2 * 40, 11) and Y.shape == (2 * 40, 3)
+    assert np.all(X[:40, 10] == 2.0) and np.all(X[40:, 10] == 5.0)
+    assert np.allclose(Y[:40], pf.mlp_targets(10, labels[0])) and np.allclose(Y[40:], pf.mlp_targets(10, labels[1]))
+    # every copy's fields are a symmetry image of the original ring's fields
+    for k in range(40):
+        assert np.isclose(np.sort(np.abs(X[k, :10])), np.sort(np.abs(ms[0].h).astype(np.float32))).all()
