@@ -1,12 +1,22 @@
 """Benchmark: eigenpairs/s of POLFED on synthetic disordered chains (one GB300 per rank).
 
-A step is one whole polfed_eigs run (spectral bounds, K from the density of
-states, block Lanczos on the Chebyshev filter with full re-orthogonalization,
-Ritz vectors, Rayleigh-Ritz with H~, residual check) on one disorder
-realization.  Ranks (torchrun) run independent realizations (weak scaling, no
-data-path collective).  Prints one JSON line on rank 0.
+The work is a stream of back-to-back polfed_eigs runs on fresh disorder
+realizations (spectral bounds, K from the density of states, block Lanczos on
+the Chebyshev filter with full re-orthogonalization, Ritz vectors,
+Rayleigh-Ritz with H~, refinement sweeps, residual check).  A *step* is one
+block-Lanczos step of that stream (one Chebyshev filter of the n_b block,
+re-orthogonalization, QR and, from some step on, the T_j eigenproblem with
+the convergence test), or one refinement sweep; the library reports every
+step boundary through its progress hook.  --warmup W steps are untimed, then
+exactly --steps K steps are timed (barrier + device synchronize on both
+sides), and the run in progress at the end is finished untimed so that its
+pairs are verified.  Each run's verified pairs are credited to the timed
+region in proportion to the share of the run's time that lies inside it.
+Ranks (torchrun) run independent realizations (weak scaling, no data-path
+collective).  Prints one JSON line on rank 0.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py --filter-only [--workload ...] [--precision f32|df64|f64] [--K 6]
 """
 from __future__ import annotations
 
@@ -19,6 +29,7 @@ import statistics
 import subprocess
 import sys
 import time
+from concurrent.futures import ThreadPoolExecutor
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -34,6 +45,9 @@ WORKLOADS = {
     "L20_j1j2_W4": (I.j1j2, 20, 4.0, 200, 32, 2),
     "L14_xxz_W3": (I.xxz, 14, 3.0, 50, 16, 1),
     "L24_j1j2_W5": (I.j1j2, 24, 5.0, 1000, 64, 5),
+    # free-fermion point (Delta = 0, J2 = 0, open chain): exact spectrum at any L
+    "L22_ff_W3": (I.free_fermion, 22, 3.0, 500, 64, 6),
+    "L24_ff_W3": (I.free_fermion, 24, 3.0, 1000, 64, 6),
 }
 # 64 XXZ rings, L = 16 / 18 alternating, W cycling {1,2,3,4,6,8}, N_ev cycling {50,100,200}
 BATCHED = {"batched64_L16_L18": (64, (16, 18), (1.0, 2.0, 3.0, 4.0, 6.0, 8.0), (50, 100, 200), 3),
@@ -61,16 +75,17 @@ def tma_kernel_source_sha():
     return hashlib.sha256(src[a:b].encode()).hexdigest()[:16]
 
 
-def step_kernel_traffic(precision):
-    """DRAM bytes per step-kernel launch from the committed ncu summary, if it
-    was taken on the current kernel source (else None)."""
+def step_kernel_traffic(precision, workload):
+    """DRAM traffic of one step-kernel launch from the committed ncu summary of
+    this workload and precision, if it was taken on the current kernel source
+    (else None)."""
     try:
         sha = tma_kernel_source_sha()
         with open(os.path.join(ROOT, "profiles", "step_kernel_traffic.json")) as f:
             d = json.load(f)
-        e = d.get(precision)
+        e = d.get(f"{workload}:{precision}")
         if e and e.get("source_sha") == sha:
-            return e
+            return {"dram_bytes_per_launch_scaled": e["dram_bytes_per_launch"], "source": e.get("summary")}
     except Exception:
         pass
     return None
@@ -122,11 +137,13 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# Chebyshev block steps (K x m) of the float32 stage for each single workload, as measured by
-# polfed_eigs on GB300 (method parameters: they follow from the density of states and N_ev,
-# not from the hardware).  The CPU estimates below multiply the oracle's time per step by them.
-KM_STEPS = {"L22_xxz_W3": (9472, 23), "L20_j1j2_W4": (5958, 20), "L14_xxz_W3": (352, 14),
-            "L24_j1j2_W5": (20000, 44)}
+# --------------------------------------------------------------- CPU oracle legs
+def host_threads():
+    """Host cores this process may use (the affinity mask, else the CPU count)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
 
 
 def oracle_dense_sample(seconds=12.0):
@@ -143,53 +160,134 @@ def oracle_dense_sample(seconds=12.0):
         if time.perf_counter() - t0 >= seconds:
             break
     dt = time.perf_counter() - t0
-    return {"value": n_pairs / dt, "unit": "eigenpairs/s", "cores": os.cpu_count(), "kind": "oracle",
+    return {"value": n_pairs / dt, "unit": "eigenpairs/s", "cores": host_threads(), "kind": "oracle",
             "sample": f"dense ED (numpy eigh, default BLAS threads) of {n_real} L=14 XXZ W=3 realizations, "
                       f"N_ev=50 each, {dt:.1f} s"}
 
 
-def oracle_filter_sample(workload, K_run=None, m_run=None, seconds=12.0, realization=0):
-    """A bounded sample of the workload itself on the host: the oracle's filter by the
-    matrix three-term recurrence (filter_matrix_powers) on the workload's sparse H~
-    (scipy CSR, single-threaded SpMM) for the workload's n_b columns, run for about
-    `seconds`; the rate is extrapolated to a whole run by its K x m block steps of the
-    float32 stage (refinement and FP64 work left out, so the CPU time is a lower bound)."""
-    import scipy.sparse as sp
+def _column_worker(conn, workload, realization, chunk, ncols):
+    """A host process that owns one column chunk of the workload's block and runs
+    the oracle's filter on it when asked (n Chebyshev steps per request)."""
     import oracle as O
     builder, L, W, n_ev, n_b, cfg = WORKLOADS[workload]
-    K, m = (K_run, m_run) if K_run else KM_STEPS[workload]
     md = builder(L, W, cfg, realization)
-    t_b0 = time.perf_counter()
     H, _ = O.sparse_hamiltonian(md.L, md.J1, md.J2, md.Delta, md.h, md.periodic)
-    t_build = time.perf_counter() - t_b0
-    nb1 = L if md.periodic else L - 1
-    nb2 = L if md.periodic else L - 2
-    bound = (nb1 * abs(md.J1) + nb2 * abs(md.J2)) * (0.5 + abs(md.Delta) / 4) + 0.5 * float(np.abs(md.h).sum())
-    Ht = (H / bound).tocsr()  # H~ for [e_lo, e_hi] = [-bound, bound] (bound >= ||H||)
-    X = I.block(H.shape[0], n_b, 11)
-    c, D = O.cheb_coeffs(0.0, 4)
-    O.filter_matrix_powers(Ht, X, c, D)  # warm-up
-    steps, t0 = 0, time.perf_counter()
-    while time.perf_counter() - t0 < seconds:
+    Ht = (H / field_free_bound(md)).tocsr()  # H~ for [e_lo, e_hi] = [-bound, bound] (bound >= ||H||)
+    X = I.block(H.shape[0], ncols, 11 + chunk)
+    conn.send("ready")
+    while True:
+        n = conn.recv()
+        if n is None:
+            break
+        c, D = O.cheb_coeffs(0.0, n)
+        t0 = time.perf_counter()
         O.filter_matrix_powers(Ht, X, c, D)
-        steps += 4
-    t_step = (time.perf_counter() - t0) / steps
-    t_run = K * m * t_step
-    return {"value": n_ev / t_run, "unit": "eigenpairs/s", "cores": 1, "kind": "oracle",
-            "sample": f"oracle filter_matrix_powers on the {workload} sparse H~ (dim {H.shape[0]}, {n_b} columns, "
-                      f"scipy CSR SpMM, 1 thread): {steps} Chebyshev steps in {steps * t_step:.1f} s "
-                      f"({t_step:.3f} s/step, H built in {t_build:.1f} s), extrapolated to the run's "
-                      f"K x m = {K} x {m} block steps of the float32 stage (a lower bound on the CPU time: "
-                      f"refinement and FP64 work left out)",
-            "seconds_per_step": t_step, "extrapolated_run_s": t_run}
+        conn.send(time.perf_counter() - t0)
+    conn.close()
+
+
+class OracleFilter:
+    """The oracle's Chebyshev filter (filter_matrix_powers: the matrix three-term
+    recurrence on a scipy CSR H~) on one realization of a workload, its n_b
+    columns split over `procs` host processes (spawned), one column chunk per
+    process (the paper's column-per-core parallelism, Supplement "Technical
+    details")."""
+
+    def __init__(self, workload, procs, realization=0):
+        import multiprocessing as mp
+        builder, L, W, n_ev, n_b, cfg = WORKLOADS[workload]
+        self.workload, self.n_ev, self.n_b, self.L = workload, n_ev, n_b, L
+        self.realization = realization
+        self.dim = math.comb(L, L // 2)
+        self.threads = max(1, min(procs, n_b))
+        sizes = [len(c) for c in np.array_split(np.arange(n_b), self.threads)]
+        ctx = mp.get_context("spawn")
+        t0 = time.perf_counter()
+        self.conns, self.procs = [], []
+        for k, nc in enumerate(sizes):
+            a, b = ctx.Pipe()
+            pr = ctx.Process(target=_column_worker, args=(b, workload, realization, k, nc), daemon=True)
+            pr.start()
+            self.conns.append(a)
+            self.procs.append(pr)
+        for a in self.conns:
+            assert a.recv() == "ready"
+        self.t_build = time.perf_counter() - t0
+
+    def steps(self, n):
+        """n Chebyshev steps of the whole block (all chunks in parallel); returns the seconds taken."""
+        t0 = time.perf_counter()
+        for a in self.conns:
+            a.send(n)
+        for a in self.conns:
+            a.recv()
+        return time.perf_counter() - t0
+
+    def rate(self, seconds, n=4):
+        """Seconds per Chebyshev step of the block, measured for about `seconds`."""
+        self.steps(n)  # warm-up
+        done, t = 0, 0.0
+        while t < seconds:
+            t += self.steps(n)
+            done += n
+        return t / done, done, t
+
+    def method_order(self, n_ev):
+        """K and block steps of a plain FP64 POLFED run of this realization, from
+        the oracle: bounds (ARPACK), exact sector moments, the Gaussian density at
+        the middle of the spectrum and the order rule for (1 + 0.2) N_ev
+        accessible values; block steps at the Supplement's convergence onset
+        m s = 2 N_ev (Fig. S1), the fewest any run needs."""
+        import oracle as O
+        builder, L, W, _, n_b, cfg = WORKLOADS[self.workload]
+        md = builder(L, W, cfg, self.realization)
+        H, _ = O.sparse_hamiltonian(md.L, md.J1, md.J2, md.Delta, md.h, md.periodic)
+        lo, hi = O.extreme_eigenvalues(H)
+        mean, var = O.sector_moments(H)
+        rho_t = O.gaussian_rho(self.dim, mean, var, 0.5 * (lo + hi)) * 0.5 * (hi - lo)
+        K = O.order_for_window(rho_t, 1.2 * n_ev)
+        m = int(math.ceil(2.0 * n_ev / self.n_b))
+        return K, m
+
+    def close(self):
+        for a in self.conns:
+            try:
+                a.send(None)
+            except Exception:
+                pass
+        for pr in self.procs:
+            pr.join(timeout=10)
+
+
+def oracle_baseline(workload, K_run, m_run, km_source, seconds=12.0):
+    """cpu_baseline of the GPU line: the oracle's filter on the workload, all host
+    threads, timed for about `seconds`; the eigenpairs/s figure extrapolates the
+    measured seconds per Chebyshev block step to K x m block steps (refinement,
+    re-orthogonalization and the other FP64 work are left out, so it is an
+    upper bound on the CPU rate)."""
+    f = OracleFilter(workload, host_threads())
+    try:
+        t_step, n, t = f.rate(seconds)
+    finally:
+        f.close()
+    run_s = K_run * m_run * t_step
+    return {"value": f.n_ev / run_s, "unit": "eigenpairs/s", "cores": f.threads, "kind": "oracle",
+            "sample": f"oracle filter_matrix_powers on the {workload} sparse H~ (dim {f.dim}, {f.n_b} columns "
+                      f"over {f.threads} processes, scipy CSR SpMM): {n} Chebyshev block steps in {t:.1f} s measured "
+                      f"({t_step:.4f} s per step); eigenpairs/s = N_ev / (K x m x that), K x m = {K_run} x {m_run} "
+                      f"({km_source}); refinement and FP64 dense work left out",
+            "seconds_per_cheb_step": t_step, "cheb_steps_timed": n, "seconds_timed": t,
+            "extrapolated_run_s": run_s}
 
 
 def oracle_batched_sample(ms, nev, sts, seconds=5.0):
     """The batched workload on the host: the oracle's filter rate per Chebyshev step for one
-    realization of each chain length (n_b = 16), extrapolated by every realization's own
-    K x m x (n_b / 16) block steps from the GPU run (a lower bound, as in oracle_filter_sample)."""
+    realization of each chain length (n_b = 16, one column chunk per thread), extrapolated by
+    every realization's own K x m x (n_b / 16) block steps from the GPU run."""
     import oracle as O
     rate = {}
+    thr = host_threads()
+    pool = ThreadPoolExecutor(max_workers=min(thr, 16))
     for md in ms:
         if md.L in rate:
             continue
@@ -197,56 +295,354 @@ def oracle_batched_sample(ms, nev, sts, seconds=5.0):
         bound = 2 * md.L * (0.5 + abs(md.Delta) / 4) + 0.5 * float(np.abs(md.h).sum())
         Ht = (H / bound).tocsr()
         X = I.block(H.shape[0], 16, 12)
+        chunks = [np.ascontiguousarray(X[:, c]) for c in np.array_split(np.arange(16), min(thr, 16))]
         c, D = O.cheb_coeffs(0.0, 4)
         steps, t0 = 0, time.perf_counter()
         while time.perf_counter() - t0 < seconds:
-            O.filter_matrix_powers(Ht, X, c, D)
+            list(pool.map(lambda x: O.filter_matrix_powers(Ht, x, c, D), chunks))
             steps += 4
         rate[md.L] = (time.perf_counter() - t0) / steps
+    pool.shutdown()
     t_run = sum(st["K"] * st["m"] * max(1, st["n_b"] // 16) * rate[md.L] for md, st in zip(ms, sts))
-    return {"value": sum(nev) / t_run, "unit": "eigenpairs/s", "cores": 1, "kind": "oracle",
-            "sample": "oracle filter_matrix_powers on one sparse H~ per chain length (16 columns, scipy CSR, "
-                      "1 thread): " + ", ".join(f"L={L}: {t:.4f} s/step" for L, t in sorted(rate.items()))
+    return {"value": sum(nev) / t_run, "unit": "eigenpairs/s", "cores": min(thr, 16), "kind": "oracle",
+            "sample": "oracle filter_matrix_powers on one sparse H~ per chain length (16 columns over "
+                      f"{min(thr, 16)} threads, scipy CSR): "
+                      + ", ".join(f"L={L}: {t:.4f} s/step" for L, t in sorted(rate.items()))
                       + f"; extrapolated by each realization's K x m block steps: {t_run:.0f} s for the batch "
-                        "(a lower bound: refinement and FP64 work left out)"}
+                        "(refinement and FP64 work left out)",
+            "extrapolated_run_s": t_run}
 
 
 def run_reference(args):
+    """--impl reference: the CPU oracle on the host cores.  Each step is a bounded
+    sample of the workload: `cheb_per_step` Chebyshev steps of the n_b block
+    through the oracle's filter, one column chunk per thread.  The eigenpairs/s
+    value extrapolates the measured seconds per Chebyshev step to the K x m
+    block steps the oracle's own order rule and the Supplement's convergence
+    onset give for this realization."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     if args.workload in BATCHED:
-        sample = lambda secs: oracle_dense_sample(secs)
-        cfg = {"workload": "L14_xxz_W3 dense-ED sample (bounded stand-in for " + args.workload + ")",
-               "N_ev": 50, "eps": 0.5}
+        wl = "L14_xxz_W3"
     else:
-        sample = lambda secs: oracle_filter_sample(args.workload, seconds=secs)
-        builder, L, W, n_ev, n_b, c_id = WORKLOADS[args.workload]
-        cfg = {"workload": args.workload, "L": L, "W": W, "N_ev": n_ev, "n_b": n_b, "eps": 0.5,
-               "estimate": "oracle filter rate extrapolated by K x m block steps"}
+        wl = args.workload
+    builder, L, W, n_ev, n_b, c_id = WORKLOADS[wl]
+    f = OracleFilter(wl, host_threads())
+    t_setup0 = time.perf_counter()
+    K, m = f.method_order(n_ev)
+    t_setup = time.perf_counter() - t_setup0
+    n_cheb = 8 if f.dim > 100000 else 64
     for _ in range(args.warmup):
-        sample(1.0)
-    vals, last = [], None
+        f.steps(n_cheb)
+    per = []
     for _ in range(args.steps):
-        last = sample(8.0)
-        vals.append(last["value"])
-    value = float(np.mean(vals))
-    cb = dict(last)
-    cb["value"] = value
-    n_ev = cfg["N_ev"]
+        per.append(f.steps(n_cheb))
+    f.close()
+    t_timed = float(sum(per))
+    t_step = t_timed / (n_cheb * args.steps)
+    run_s = K * m * t_step
+    value = n_ev / run_s
+    cfg = {"workload": wl, "L": L, "W": W, "N_ev": n_ev, "n_b": n_b, "eps": 0.5, "dim": f.dim,
+           "step": f"{n_cheb} Chebyshev steps of the {n_b}-column block (oracle filter, {f.threads} processes)",
+           "K": K, "m": m,
+           "K_m_source": "oracle: ARPACK bounds, exact sector moments, Gaussian density, order rule for 1.2 N_ev; "
+                         "m s = 2 N_ev (convergence onset of the Supplement)"}
+    if args.workload in BATCHED:
+        cfg["stand_in_for"] = args.workload
+    cb = {"value": value, "unit": "eigenpairs/s", "cores": f.threads, "kind": "oracle",
+          "sample": f"{args.steps} timed steps of {n_cheb} Chebyshev block steps each on {wl} (dim {f.dim}): "
+                    f"{t_step:.4f} s per Chebyshev step measured; eigenpairs/s extrapolated by K x m = {K} x {m}",
+          "seconds_per_cheb_step": t_step, "extrapolated_run_s": run_s, "setup_s": round(t_setup + f.t_build, 2)}
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "eigenpairs/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * n_ev / value,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * t_timed / args.steps, 2),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": cfg, "cpu_baseline": cb,
             "e2e": {"value": value, "unit": "eigenpairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ GPU arm
+class StepWindow:
+    """Counts step boundaries reported by the library's progress hook and takes
+    the timed region: after `warmup` boundaries it synchronizes, passes a
+    barrier and records a CUDA event on the context's stream, the wall clock and
+    the library's counters; after `warmup + steps` boundaries it does the same
+    to close the region."""
+
+    def __init__(self, torch, pf, stream, warmup, steps, dist, clocks):
+        self.torch, self.pf, self.stream = torch, pf, stream
+        self.W, self.K = warmup, steps
+        self.dist, self.clocks = dist, clocks
+        self.n = 0
+        self.ev = {"ref": self.event(), "start": None, "stop": None}
+        self.ev["ref"].record(stream)
+        self.wall = {}
+        self.cnt = {}
+
+    def event(self):
+        return self.torch.cuda.Event(enable_timing=True)
+
+    def ms(self, e):
+        """Offset of event e from the reference event, ms (same stream: a common timeline)."""
+        return self.ev["ref"].elapsed_time(e)
+
+    @property
+    def started(self):
+        return self.ev["start"] is not None
+
+    @property
+    def done(self):
+        return self.ev["stop"] is not None
+
+    def hook(self, phase, index):
+        if phase not in (self.pf.PHASE_BLOCK, self.pf.PHASE_REFINE):
+            return
+        self.n += 1
+        if self.n == self.W:
+            self.open()
+        elif self.n == self.W + self.K:
+            self.close()
+
+    def open(self):
+        self.torch.cuda.synchronize()
+        if self.dist:
+            self.dist.barrier()
+        if self.clocks:
+            self.clocks.start()
+        self.cnt["start"] = self.pf.get_counters()
+        self.wall["start"] = time.perf_counter()
+        e = self.event()
+        e.record(self.stream)
+        self.ev["start"] = e
+
+    def close(self):
+        e = self.event()
+        e.record(self.stream)
+        self.torch.cuda.synchronize()
+        self.wall["stop"] = time.perf_counter()
+        self.cnt["stop"] = self.pf.get_counters()
+        self.ev["stop"] = e
+        if self.dist:
+            self.dist.barrier()
+
+
+def overlap(a0, a1, b0, b1):
+    return max(0.0, min(a1, b1) - max(a0, b0))
+
+
+def credited_pairs(spans, w0, w1):
+    """Eigenpairs credited to the timed region [w0, w1]: each run (start, end,
+    verified pairs) contributes its pairs times the share of its span inside
+    the region."""
+    return sum(ok * overlap(s, e, w0, w1) / max(e - s, 1e-12) for s, e, ok in spans)
+
+
+def run_single(args, pf, torch, dev, world, rank, local, dist):
+    builder, L, W, n_ev, n_b, cfg = WORKLOADS[args.workload]
+    dim = pf.basis_build(L, L // 2)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = pf.Ctx(local)
+    ctx.set_stream(stream)
+    opts = pf.opts_default()
+    opts.precision = PREC[args.precision]
+    opts.dos_rule = DOS[args.dos]
+    net, mlp_info = None, None
+    if args.dos == "mlp":
+        net, mlp_info = train_predictor(pf, ctx, builder, L, W, cfg)
+    evecs = torch.empty((n_ev, dim), dtype=torch.float64, device=dev)  # column-major dim x N_ev
+    host_evecs = torch.empty((n_ev, dim), dtype=torch.float64, pin_memory=True)
+    fields_pinned = torch.empty(L, dtype=torch.float64, pin_memory=True)
+    clocks = Clocks(local) if rank == 0 else None
+    win = StepWindow(torch, pf, stream, args.warmup, args.steps, dist, clocks)
+    ctx.set_progress(win.hook)
+    torch.cuda.synchronize()
+    if win.W == 0:
+        win.open()
+    runs = []
+    r = 0
+    while not win.done:
+        m = builder(L, W, cfg, timed_realization(r, world, rank))
+        e_s, e_e = win.event(), win.event()
+        t_s = time.perf_counter()
+        e_s.record(stream)
+        fields_pinned.copy_(torch.from_numpy(m.h))
+        model = pf.Model(L, m.J1, m.J2, m.Delta, fields_pinned.numpy(), m.periodic)
+        if net is not None:  # the learned predictor sets K (inference inside the run)
+            emin, emax, rho = net.predict(model, W)
+            opts.rho_hint = rho
+            w = emax - emin
+            opts.emin_hint, opts.emax_hint = emin - 0.02 * w, emax + 0.02 * w
+        ev, res, st, rc = pf.eigs(ctx, model, 0.5, n_ev, 0, n_b, opts, d_evecs=evecs, allow_noconv=True)
+        e_e.record(stream)
+        with torch.cuda.stream(stream):
+            host_evecs.copy_(evecs, non_blocking=True)
+        stream.synchronize()
+        t_e = time.perf_counter()
+        hn = max(abs(st["E_min"]), abs(st["E_max"]))
+        ok = int(np.sum(res[: len(ev)] <= 1e-8 * hn)) if rc == 0 else 0
+        runs.append({"realization": timed_realization(r, world, rank), "ev_s": e_s, "ev_e": e_e, "t_s": t_s,
+                     "t_e": t_e, "ok": ok, "rc": rc, "st": st, "max_rel_resid": float(np.max(res) / hn),
+                     "evals": ev})
+        r += 1
+    ctx.set_progress(None)
+    torch.cuda.synchronize()
+    ck = clocks.stop() if clocks else None
+    # timed region on the device timeline and on the wall clock
+    w0, w1 = win.ms(win.ev["start"]), win.ms(win.ev["stop"])
+    t_dev = (w1 - w0) / 1e3
+    t_wall = win.wall["stop"] - win.wall["start"]
+    h2d, d2h, in_window = 0, 0, []
+    for run in runs:
+        run["s"], run["e"] = win.ms(run["ev_s"]), win.ms(run["ev_e"])
+    pairs_dev = credited_pairs([(x["s"], x["e"], x["ok"]) for x in runs], w0, w1)
+    pairs_wall = credited_pairs([(x["t_s"], x["t_e"], x["ok"]) for x in runs], win.wall["start"], win.wall["stop"])
+    for run in runs:
+        s, e = run["s"], run["e"]
+        od = overlap(s, e, w0, w1)
+        ow = overlap(run["t_s"], run["t_e"], win.wall["start"], win.wall["stop"])
+        if od > 0 or ow > 0:
+            in_window.append(run)
+        if win.wall["start"] <= run["t_s"] <= win.wall["stop"]:
+            h2d += L * 8
+        if win.wall["start"] <= run["t_e"] <= win.wall["stop"]:
+            d2h += n_ev * dim * 8 + 2 * n_ev * 8
+        run["dev_s"] = (e - s) / 1e3
+        run["wall_s"] = run["t_e"] - run["t_s"]
+        run["share_in_window"] = od / max(e - s, 1e-9)
+    t_dev, t_wall, pairs_all, pairs_wall_all = reduce_ranks(torch, dev, dist, t_dev, t_wall, pairs_dev, pairs_wall)
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    c0, c1 = win.cnt["start"], win.cnt["stop"]
+    peak, peak_kind = peaks()
+    names = {0: "f64", 1: "f32", 2: "df64"}
+    kinds = {}
+    for k in range(3):
+        n = c1["kind_launches"][k] - c0["kind_launches"][k]
+        g = c1["kind_gpu_s"][k] - c0["kind_gpu_s"][k]
+        b = c1["kind_alg_bytes"][k] - c0["kind_alg_bytes"][k]
+        if n > 0 and g > 0:
+            kinds[names[k]] = {"launches": int(n), "avg_launch_us": round(1e6 * g / n, 2),
+                               "alg_bytes_per_launch": b / n, "achieved_gbs": round(b / g / 1e9, 1),
+                               "share_of_step": round(g / max(t_dev, 1e-12), 4)}
+    dom = max(kinds, key=lambda k: kinds[k]["share_of_step"]) if kinds else args.precision
+    d = kinds.get(dom, {"achieved_gbs": 0.0, "alg_bytes_per_launch": 0.0, "avg_launch_us": 0.0, "launches": 0,
+                        "share_of_step": 0.0})
+    tr = step_kernel_traffic(dom, args.workload)
+    roof = {"bound": "hbm", "achieved": d["achieved_gbs"], "peak": peak, "unit": "GB/s",
+            "frac": round(d["achieved_gbs"] / peak, 4),
+            "traffic": (tr or {}).get("dram_bytes_per_launch_scaled"),
+            "peak_kind": f"of {peak_kind}",
+            "kernel": f"k_ham_step_tma<{dom}> (Clenshaw step on a 128-byte column slice)",
+            "alg_bytes_per_launch": d["alg_bytes_per_launch"], "avg_launch_us": d["avg_launch_us"],
+            "launches": d["launches"], "share_of_step": d["share_of_step"], "by_kind": kinds}
+    if tr:
+        roof["traffic_source"] = tr.get("source")
+    value = pairs_all / t_dev
+    line = {"metric": METRIC, "value": round(value, 4), "unit": "eigenpairs/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * t_dev / args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
+            "data": "synthetic",
+            "config": {"workload": args.workload, "L": L, "dim": dim, "hamiltonian": builder.__name__,
+                       "W": W, "N_ev": n_ev, "n_b": n_b, "eps": 0.5, "dos_rule": args.dos,
+                       "step": "one block-Lanczos step or refinement sweep of back-to-back polfed_eigs runs",
+                       "pairs_credited": round(pairs_all, 2),
+                       "runs": [{"realization": x["realization"], "K": x["st"]["K"], "m": x["st"]["m"],
+                                 "refine": x["st"]["n_refine"], "restarts": x["st"]["n_restarts"],
+                                 "fallback_df64": x["st"]["fallback_df64"], "status": x["rc"],
+                                 "verified_pairs": x["ok"], "max_resid_over_normH": x["max_rel_resid"],
+                                 "dev_s": round(x["dev_s"], 3), "wall_s": round(x["wall_s"], 3),
+                                 "share_in_window": round(x["share_in_window"], 4),
+                                 "phase_s": {k[2:]: round(x["st"][k], 2) for k in
+                                             ("t_bounds", "t_filter", "t_reorth", "t_qr", "t_teig", "t_ritz",
+                                              "t_total")}}
+                                for x in runs],
+                       "parallelism": f"replicas x{world}",
+                       "l2": "per-step working set (>= 3 x 90 MB slices + 10 GB Lanczos basis) >> L2, no flush"},
+            "roofline": roof,
+            "e2e": {"value": round(pairs_wall_all / t_wall, 4), "unit": "eigenpairs/s",
+                    "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps},
+            "gpu_launches": int(c1["launches"] - c0["launches"]),
+            "clocks": ck}
+    if mlp_info:
+        line["config"]["mlp"] = mlp_info
+    if world == 1 and not args.no_cpu_baseline:
+        Ks = [x["st"]["K"] for x in in_window] or [runs[-1]["st"]["K"]]
+        ms_ = [x["st"]["m"] for x in in_window] or [runs[-1]["st"]["m"]]
+        line["cpu_baseline"] = oracle_baseline(args.workload, int(round(np.mean(Ks))), int(round(np.mean(ms_))),
+                                               "mean K and m of the timed GPU runs")
+        if L > 14:
+            line["cpu_dense_ed_L14"] = oracle_dense_sample(8.0)
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_filter_only(args, pf, torch, dev):
+    """One polfed_cheb_filter call (sigma = 0, order --K) on a seeded block of the
+    workload's Hamiltonian, for kernel profiling (ncu): K + 1 step-kernel launches
+    per 128-byte column slice.  Batched workloads: one polfed_cheb_filter_batched
+    call over their realizations (n_b = 16)."""
+    kind = PREC[args.precision]
+    dt = torch.float32 if kind == pf.F32 else torch.float64
+    if args.workload in BATCHED:
+        n, Ls, Wc, Nc, cfg = BATCHED[args.workload]
+        ms, Xs, Ys = [], [], []
+        for r in range(n):
+            m = I.xxz(Ls[r % len(Ls)], Wc[r % len(Wc)], cfg, r)
+            d = pf.basis_build(m.L, m.L // 2)
+            ms.append(m)
+            Xs.append(torch.from_numpy(I.block(d, 16, 100 + r)).to(dev, dt))
+            Ys.append(torch.empty_like(Xs[-1]))
+        bound = [field_free_bound(m) for m in ms]
+        pf.cheb_filter_batched(ms, [-b for b in bound], bound, [0.0] * n, [args.K] * n, Xs, Ys, 16, kind)
+        torch.cuda.synchronize()
+        print(f"filter-only ok: batched {args.workload} {args.precision} K={args.K}")
+        return
+    builder, L, W, n_ev, n_b, cfg = WORKLOADS[args.workload]
+    m = builder(L, W, cfg, 0)
+    dim = pf.basis_build(L, L // 2)
+    st = torch.empty(dim, dtype=torch.int32, device=dev)
+    pf.basis_build(L, L // 2, st)
+    X = torch.from_numpy(I.block(dim, n_b, 7)).to(dev, dt)
+    Y = torch.empty_like(X)
+    b = field_free_bound(m)
+    reps = max(1, args.reps)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    c0 = pf.get_counters()
+    torch.cuda.synchronize()
+    ev0.record()
+    for _ in range(reps):
+        pf.cheb_filter(m, st, dim, -b, b, 0.0, args.K, X, Y, n_b, kind)
+    ev1.record()
+    torch.cuda.synchronize()
+    c1 = pf.get_counters()
+    k = {pf.F64: 0, pf.F32: 1, pf.DF64: 2}[kind]
+    n = c1["kind_launches"][k] - c0["kind_launches"][k]
+    g = c1["kind_gpu_s"][k] - c0["kind_gpu_s"][k]
+    a = c1["kind_alg_bytes"][k] - c0["kind_alg_bytes"][k]
+    print(json.dumps({"filter_only": args.workload, "precision": args.precision, "K": args.K, "n_b": n_b,
+                      "dim": dim, "reps": reps, "call_ms": round(ev0.elapsed_time(ev1) / reps, 3),
+                      "step_launches": int(n), "avg_step_us": round(1e6 * g / max(n, 1), 2),
+                      "alg_gbs": round(a / max(g, 1e-12) / 1e9, 1),
+                      "frac_of_peak": round(a / max(g, 1e-12) / 1e9 / peaks()[0], 4)}), flush=True)
+
+
+def field_free_bound(m):
+    """A bound on ||H|| for Eq. (1): each bond term is at most |J_l| (1/2 + |Delta|/4), each field term |h_i|/2."""
+    nb1 = m.L if m.periodic else m.L - 1
+    nb2 = m.L if m.periodic else m.L - 2
+    return 1.01 * ((nb1 * abs(m.J1) + nb2 * abs(m.J2)) * (0.5 + abs(m.Delta) / 4) + 0.5 * float(np.abs(m.h).sum()))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="L22_xxz_W3", choices=sorted(WORKLOADS) + sorted(BATCHED))
     ap.add_argument("--precision", default=None, choices=sorted(PREC),
@@ -256,10 +652,13 @@ def main():
     ap.add_argument("--batch-mode", default="batched", choices=["batched", "sequential"],
                     help="batched workloads: one polfed_eigs_batched call, or polfed_eigs per realization")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--filter-only", action="store_true", help="one filter call (kernel profiling)")
+    ap.add_argument("--K", type=int, default=6, help="--filter-only: filter order")
+    ap.add_argument("--reps", type=int, default=1, help="--filter-only: filter calls")
     args = ap.parse_args()
     if args.precision is None:
         args.precision = "df64" if args.workload in BATCHED else "f32"
-    if args.warmup < 3:
+    if args.warmup < 3 and not args.filter_only:
         print("warning: fewer than 3 warm-up steps; the number is not valid", file=sys.stderr)
     if args.impl == "reference":
         run_reference(args)
@@ -280,160 +679,38 @@ def main():
     __graft_entry__.build()
     import paper_2005_09534_gb300 as pf
 
-    if args.workload in BATCHED:
+    if args.filter_only:
+        run_filter_only(args, pf, torch, dev)
+    elif args.workload in BATCHED:
         run_batched(args, pf, torch, dev, world, rank, local, dist)
-        return
-    builder, L, W, n_ev, n_b, cfg = WORKLOADS[args.workload]
-    dim = pf.basis_build(L, L // 2)
-    stream = torch.cuda.Stream(device=dev)
-    ctx = pf.Ctx(local)
-    ctx.set_stream(stream)
-    opts = pf.opts_default()
-    opts.precision = PREC[args.precision]
-    opts.dos_rule = DOS[args.dos]
-    net, mlp_info = None, None
-    if args.dos == "mlp":
-        net, mlp_info = train_predictor(pf, ctx, builder, L, W)
-    evecs = torch.empty((n_ev, dim), dtype=torch.float64, device=dev)  # column-major dim x N_ev
-    host_evecs = torch.empty((n_ev, dim), dtype=torch.float64, pin_memory=True)
-    fields_pinned = torch.empty(L, dtype=torch.float64, pin_memory=True)
-
-    def one(realization, copy_out):
-        m = builder(L, W, cfg, realization)
-        fields_pinned.copy_(torch.from_numpy(m.h))
-        model = pf.Model(L, m.J1, m.J2, m.Delta, fields_pinned.numpy(), m.periodic)
-        if net is not None:  # the learned predictor sets K (inference inside the timed step)
-            emin, emax, rho = net.predict(model, W)
-            opts.rho_hint = rho
-            w = emax - emin
-            opts.emin_hint, opts.emax_hint = emin - 0.02 * w, emax + 0.02 * w
-        ev, res, st, rc = pf.eigs(ctx, model, 0.5, n_ev, 0, n_b, opts, d_evecs=evecs, allow_noconv=True)
-        hn = max(abs(st["E_min"]), abs(st["E_max"]))
-        ok = int(np.sum(res[: len(ev)] <= 1e-8 * hn)) if rc == 0 else 0
-        return ok, st, rc, float(np.max(res) / hn)
-
-    for w in range(args.warmup):
-        one(warmup_realization(w, world, rank), False)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    clocks = Clocks(local)
-    if rank == 0:
-        clocks.start()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    dev_ms, wall_s, pairs = 0.0, 0.0, 0
-    agg = {"n_launches": 0, "n_step_launches": 0, "step_gpu_s": 0.0, "step_alg_bytes": 0.0, "K": [], "m": [],
-           "max_rel_resid": 0.0, "status": [], "restarts": [], "refine": []}
-    torch.cuda.synchronize()
-    for k in range(args.steps):
-        t0 = time.perf_counter()
-        e0.record(stream)
-        ok, st, rc, rr = one(timed_realization(k, world, rank), True)
-        e1.record(stream)
-        with torch.cuda.stream(stream):
-            host_evecs.copy_(evecs, non_blocking=True)
-        stream.synchronize()
-        wall_s += time.perf_counter() - t0
-        dev_ms += e0.elapsed_time(e1)
-        pairs += ok
-        for key in ("n_launches", "n_step_launches", "step_gpu_s", "step_alg_bytes"):
-            agg[key] += st[key]
-        for key in ("kind_launches", "kind_gpu_s", "kind_alg_bytes"):
-            agg.setdefault(key, [0, 0, 0])
-            agg[key] = [a + b for a, b in zip(agg[key], st[key])]
-        agg["K"].append(st["K"])
-        agg["m"].append(st["m"])
-        agg["status"].append(rc)
-        agg["restarts"].append(st["n_restarts"])
-        agg["refine"].append(st["n_refine"])
-        for key in ("t_bounds", "t_filter", "t_reorth", "t_qr", "t_teig", "t_ritz", "t_total"):
-            agg.setdefault(key, 0.0)
-            agg[key] += st[key]
-        agg["max_rel_resid"] = max(agg["max_rel_resid"], rr)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    ck = clocks.stop() if rank == 0 else None
-    t_dev, wall_s, pairs_all = reduce_ranks(torch, dev, dist, dev_ms / 1e3, wall_s, pairs)
-    if rank != 0:
-        if dist:
-            dist.destroy_process_group()
-        return
-
-    peak, peak_kind = peaks()
-    # the dominant step kernel: the storage kind with the most event-timed device time
-    names = {0: "f64", 1: "f32", 2: "df64"}
-    kinds = {}
-    for k in range(3):
-        n, g, b = agg["kind_launches"][k], agg["kind_gpu_s"][k], agg["kind_alg_bytes"][k]
-        if n > 0 and g > 0:
-            kinds[names[k]] = {"launches": int(n), "avg_launch_us": round(1e6 * g / n, 2),
-                               "alg_bytes_per_launch": b / n, "achieved_gbs": round(b / g / 1e9, 1),
-                               "share_of_step": round(g / max(t_dev, 1e-12), 4)}
-    dom = max(kinds, key=lambda k: kinds[k]["share_of_step"]) if kinds else args.precision
-    d = kinds.get(dom, {"achieved_gbs": 0.0, "alg_bytes_per_launch": 0.0, "avg_launch_us": 0.0, "launches": 0,
-                        "share_of_step": 0.0})
-    tr = step_kernel_traffic(dom)
-    roof = {"bound": "hbm", "achieved": d["achieved_gbs"], "peak": peak, "unit": "GB/s",
-            "frac": round(d["achieved_gbs"] / peak, 4), "traffic": (tr or {}).get("dram_bytes_per_launch"),
-            "peak_kind": f"of {peak_kind}",
-            "kernel": f"k_ham_step_tma<{dom}> (Clenshaw step on a 128-byte column slice)",
-            "alg_bytes_per_launch": d["alg_bytes_per_launch"], "avg_launch_us": d["avg_launch_us"],
-            "launches": d["launches"], "share_of_step": d["share_of_step"], "by_kind": kinds}
-    value = pairs_all / t_dev
-    bytes_d2h = n_ev * dim * 8 + 2 * n_ev * 8
-    line = {"metric": METRIC, "value": round(value, 4), "unit": "eigenpairs/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * t_dev / args.steps, 1),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
-            "data": "synthetic",
-            "config": {"workload": args.workload, "L": L, "dim": dim, "hamiltonian": builder.__name__,
-                       "W": W, "N_ev": n_ev, "n_b": n_b, "eps": 0.5, "dos_rule": args.dos, "K": agg["K"],
-                       "m": agg["m"], "restarts": agg["restarts"], "refine_sweeps": agg["refine"],
-                       "parallelism": f"replicas x{world}", "l2": "per-step working set >> L2, no flush",
-                       "status": agg["status"], "max_resid_over_normH": agg["max_rel_resid"],
-                       "phase_s": {k[2:]: round(agg[k], 2) for k in ("t_bounds", "t_filter", "t_reorth", "t_qr",
-                                                                       "t_teig", "t_ritz", "t_total") if k in agg}},
-            "roofline": roof,
-            "e2e": {"value": round(pairs_all / wall_s, 4), "unit": "eigenpairs/s",
-                    "h2d_bytes_per_step": L * 8, "d2h_bytes_per_step": bytes_d2h},
-            "gpu_launches": int(agg["n_launches"]),
-            "clocks": ck}
-    if mlp_info:
-        line["config"]["mlp"] = mlp_info
-    if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = oracle_filter_sample(args.workload, K_run=int(np.mean(agg["K"])),
-                                                    m_run=int(round(np.mean(agg["m"]))))
-        if L > 14:
-            line["cpu_dense_ed_L14"] = oracle_dense_sample(8.0)
-    print(json.dumps(line), flush=True)
-    ctx.close()
-    if dist:
-        dist.destroy_process_group()
+    else:
+        run_single(args, pf, torch, dev, world, rank, local, dist)
 
 
 def timed_realization(k, world, rank):
-    """Realization index of timed step k on this rank (ranks never share one)."""
+    """Realization index of run k on this rank (ranks never share one)."""
     return k * world + rank
 
 
 def warmup_realization(w, world, rank):
-    """Realization index of warm-up step w on this rank (disjoint from timed ones)."""
+    """Realization index of warm-up run w on this rank (disjoint from timed ones)."""
     return 10_000 + w * world + rank
 
 
-def reduce_ranks(torch, dev, dist, t_dev, wall_s, pairs):
-    """Max of the times and sum of the eigenpairs over ranks."""
+def reduce_ranks(torch, dev, dist, t_dev, wall_s, pairs, pairs_wall=None):
+    """Max of the times and sum of the (credited) eigenpairs over ranks."""
+    if pairs_wall is None:
+        pairs_wall = pairs
     if not dist:
-        return t_dev, wall_s, pairs
-    tt = torch.tensor([t_dev, wall_s], device=dev)
+        return t_dev, wall_s, pairs, pairs_wall
+    tt = torch.tensor([t_dev, wall_s], device=dev, dtype=torch.float64)
     dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-    pp = torch.tensor([pairs], device=dev, dtype=torch.float64)
+    pp = torch.tensor([pairs, pairs_wall], device=dev, dtype=torch.float64)
     dist.all_reduce(pp)
-    return float(tt[0]), float(tt[1]), int(pp.item())
+    return float(tt[0]), float(tt[1]), float(pp[0]), float(pp[1])
 
 
-def train_predictor(pf, ctx, builder, L, W, n_real=64):
+def train_predictor(pf, ctx, builder, L, W, cfg_id, n_real=48, steps=4000):
     """Train the spectral predictor on labels the library produces (Lanczos
     bounds, KPM counts) for n_real realizations at W' in [W/2, 3W/2] (field
     config 90, disjoint from the timed realizations).  Untimed setup."""
@@ -442,15 +719,16 @@ def train_predictor(pf, ctx, builder, L, W, n_real=64):
     models, Ws = [], []
     for k in range(n_real):
         w = W * (0.5 + ((0.6180339887498949 * (k + 1)) % 1.0))
-        models.append(builder(L, w, 90, k))
+        m = builder(L, w, 90, k)
+        models.append(m)
         Ws.append(w)
     labels = predictor.labels_for(ctx, models)
     t1 = time.perf_counter()
     X, Y = predictor.dataset(models, Ws, labels)
     net = pf.MLP(L + 1, 128, 3, seed=7)
-    loss, secs = predictor.fit(net, X, Y, steps=6000, lr=2e-3, batch=256)
+    loss, secs = predictor.fit(net, X, Y, steps=steps, lr=2e-3, batch=256)
     return net, {"train_realizations": n_real, "samples": int(X.shape[0]), "label_s": round(t1 - t0, 1),
-                 "train_s": round(secs, 1), "train_loss": round(float(loss), 4)}
+                 "train_s": round(secs, 1), "train_steps": steps, "train_loss": round(float(loss), 4)}
 
 
 def batched_models(spec, base_realization):
@@ -531,7 +809,7 @@ def run_batched(args, pf, torch, dev, world, rank, local, dist):
     if dist:
         dist.barrier()
     ck = clocks.stop() if rank == 0 else None
-    t_dev, wall_s, pairs_all = reduce_ranks(torch, dev, dist, dev_s, wall_s, pairs)
+    t_dev, wall_s, pairs_all, _ = reduce_ranks(torch, dev, dist, dev_s, wall_s, pairs)
     if rank != 0:
         if dist:
             dist.destroy_process_group()

@@ -210,6 +210,44 @@ void polfed_ctx_destroy(polfed_ctx* ctx);
 /* Stream used by the context's calls (NULL before any call = its own stream). */
 int polfed_ctx_set_stream(polfed_ctx* ctx, polfed_stream_t stream);
 
+/* Phase boundaries of a polfed_eigs run, reported to the progress hook.  The
+ * paper's run is a sequence of block-Lanczos steps (Eqs. (3)-(4): one
+ * Chebyshev filter of the block, re-orthogonalization, QR and, from some
+ * step on, the T_j eigenproblem with the convergence test and the Ritz
+ * vectors); the mixed-precision form appends refinement sweeps. */
+enum {
+  POLFED_PHASE_START = 0,  /* bounds and K chosen; index = K */
+  POLFED_PHASE_BLOCK = 1,  /* block-Lanczos step finished; index = j (0-based), counted over restarts */
+  POLFED_PHASE_REFINE = 2, /* refinement sweep finished; index = sweep (0-based) */
+  POLFED_PHASE_END = 3     /* results written; index = final status */
+};
+
+/* Progress hook: fn(user, phase, index) is called on the calling host thread
+ * of polfed_eigs / polfed_block_lanczos at every phase boundary above, after
+ * the context's stream has been synchronized, so a caller can time whole
+ * steps of the method (CUDA events on that stream, wall clocks) or log
+ * progress.  fn must not call into this library with the same context.
+ * fn = NULL removes the hook.  Not used by the batched runner. */
+typedef void (*polfed_progress_fn)(void* user, int32_t phase, int32_t index);
+int polfed_ctx_set_progress(polfed_ctx* ctx, polfed_progress_fn fn, void* user);
+
+/* Process counters of this library's device work issued by the calling host
+ * thread since it first called the library (monotone; take differences):
+ * kernel launches, and the Chebyshev step kernels' launches, device time
+ * (CUDA events around each run of step launches, on the launching stream) and
+ * algorithmic bytes N * cols * w * (3 + [c_k != 0]), in all and by storage
+ * kind (index POLFED_F64 / POLFED_F32 / POLFED_DF64). */
+typedef struct polfed_counters {
+  int64_t launches;
+  int64_t step_launches;
+  double step_gpu_s;
+  double step_alg_bytes;
+  int64_t kind_launches[3];
+  double kind_gpu_s[3];
+  double kind_alg_bytes[3];
+} polfed_counters;
+int polfed_get_counters(polfed_counters* out);
+
 /* Block Lanczos on P^K_sigma(H~), Eqs. (3)-(4), with full
  * re-orthogonalization of U_j against Q_1..Q_j, QR by Cholesky QR (twice),
  * convergence by ||B_{j+1} t~_i|| for theta_i >= p, Ritz vectors

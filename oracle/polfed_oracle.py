@@ -16,8 +16,12 @@ What each function follows (paper's numbering):
                                  T_n(x) = cos(n arccos x), D such that P(sigma) = 1.
   * ``filter_spectral``       -- P(H~) X = V diag(P(lambda~)) V^T X (definition of a
                                  matrix function; a different algorithm from Clenshaw).
-  * ``gamma_dos`` / ``choose_K`` -- order selection from the density of states with
-                                 p = 0.17 ("POLFED algorithm"; Suppl. "Convergence").
+  * ``gamma_paper``, ``sector_moments``, ``gaussian_rho``, ``lobe_halfwidth``,
+    ``n_accessible``, ``order_for_window`` -- order selection from the density of
+                                 states with p = 0.17 ("POLFED algorithm"; Suppl.
+                                 "Convergence of POLFED").
+  * ``extreme_eigenvalues``   -- E_min, E_max of a sparse H (the Lanczos bounds of the
+                                 "POLFED algorithm" paragraph, by ARPACK).
   * ``eigs_nearest``          -- the result POLFED reaches: the N_ev eigenpairs nearest
                                  the target (the text after Eqs. (3)-(4)).
   * ``gap_ratio``             -- mean gap ratio r (section "Entanglement entropy and
@@ -342,6 +346,73 @@ def n_accessible(rho_t: float, sigma: float, K: int, p: float = P_THRESHOLD) -> 
     density of states rho~ (eigenvalues per unit of the rescaled axis)."""
     xl, xr = lobe_halfwidth(sigma, K, p)
     return rho_t * (xr - xl)
+
+
+def sector_moments(H) -> Tuple[float, float]:
+    """Mean and variance of the spectrum of the sector matrix from traces:
+    Tr H / N and Tr H^2 / N - mean^2 (H dense or scipy sparse; no eigen-solve)."""
+    n = H.shape[0]
+    if hasattr(H, "multiply"):
+        t1 = float(H.diagonal().sum())
+        t2 = float(H.multiply(H).sum())
+    else:
+        t1 = float(np.trace(H))
+        t2 = float(np.sum(H * H))
+    mean = t1 / n
+    return mean, t2 / n - mean * mean
+
+
+def gaussian_rho(n_states: int, mean: float, var: float, E: float) -> float:
+    """Gaussian density of states per unit of energy at E with the spectrum's
+    mean and variance (the Supplement's estimate of the density, with the
+    width taken from the exact moments)."""
+    g = math.sqrt(var)
+    return n_states / (math.sqrt(2.0 * math.pi) * g) * math.exp(-0.5 * (E - mean) ** 2 / var)
+
+
+def dirichlet_halfwidth(K: int, p: float = P_THRESHOLD) -> float:
+    """At sigma = 0 and even K, P(sin u) = sin((K+1)u) / ((K+1) sin u): the main
+    lobe P >= p is |x| <= sin(u*) with u* the first root of that ratio = p."""
+    a, b = 1e-12, math.pi / (K + 1)
+    for _ in range(200):
+        m = 0.5 * (a + b)
+        if math.sin((K + 1) * m) / ((K + 1) * math.sin(m)) > p:
+            a = m
+        else:
+            b = m
+    return math.sin(0.5 * (a + b))
+
+
+def order_for_window(rho_t: float, n_target: float, p: float = P_THRESHOLD) -> int:
+    """Order K of the transform at sigma = 0 ("POLFED algorithm": K is chosen so
+    that about n_target eigenvalues have P >= p): the largest even K whose main
+    lobe holds at least n_target eigenvalues of a locally flat density rho_t
+    (eigenvalues per unit of the rescaled axis), lobe from ``dirichlet_halfwidth``."""
+    def holds(K):
+        return 2.0 * dirichlet_halfwidth(K, p) * rho_t >= n_target
+    if not holds(2):
+        return 2
+    lo, hi = 2, 4
+    while holds(hi):
+        lo, hi = hi, 2 * hi
+    while hi - lo > 2:  # even K: holds(lo), not holds(hi)
+        mid = (lo + hi) // 2
+        mid -= mid % 2
+        if holds(mid):
+            lo = mid
+        else:
+            hi = mid
+    return lo
+
+
+def extreme_eigenvalues(H) -> Tuple[float, float]:
+    """Lowest and highest eigenvalue of a sparse symmetric H (ARPACK Lanczos,
+    scipy.sparse.linalg.eigsh), the spectral bounds E0, E1 of the "POLFED
+    algorithm" paragraph."""
+    from scipy.sparse.linalg import eigsh
+    lo = eigsh(H, k=1, which="SA", return_eigenvectors=False, tol=1e-12)[0]
+    hi = eigsh(H, k=1, which="LA", return_eigenvectors=False, tol=1e-12)[0]
+    return float(lo), float(hi)
 
 
 # ----------------------------------------------------------------------------

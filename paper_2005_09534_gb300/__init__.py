@@ -29,9 +29,15 @@ F64, F32, DF64 = 0, 1, 2
 
 DOS_MOMENTS, DOS_GAMMA, DOS_KPM, DOS_HINT = 0, 1, 2, 3
 
+PHASE_START, PHASE_BLOCK, PHASE_REFINE, PHASE_END = 0, 1, 2, 3
+
+# void (*)(void* user, int32_t phase, int32_t index)
+PROGRESS_FN = ctypes.CFUNCTYPE(None, c_void_p, c_int32, c_int32)
+
 EXPORTED = ["polfed_opts_default", "polfed_basis_build", "polfed_h_apply", "polfed_cheb_filter",
             "polfed_cheb_filter_static",
-            "polfed_ctx_create", "polfed_ctx_destroy", "polfed_ctx_set_stream", "polfed_block_lanczos",
+            "polfed_ctx_create", "polfed_ctx_destroy", "polfed_ctx_set_stream", "polfed_ctx_set_progress",
+            "polfed_get_counters", "polfed_block_lanczos",
             "polfed_eigs", "polfed_spectral_bounds", "polfed_kpm_moments", "polfed_kpm_count",
             "polfed_spectral_labels", "polfed_mlp_create", "polfed_mlp_destroy", "polfed_mlp_num_params",
             "polfed_mlp_set_params", "polfed_mlp_get_params", "polfed_mlp_set_scaling", "polfed_mlp_forward",
@@ -79,6 +85,15 @@ class CStats(ctypes.Structure):
         return d
 
 
+class CCounters(ctypes.Structure):
+    _fields_ = [("launches", c_int64), ("step_launches", c_int64), ("step_gpu_s", c_double),
+                ("step_alg_bytes", c_double), ("kind_launches", c_int64 * 3), ("kind_gpu_s", c_double * 3),
+                ("kind_alg_bytes", c_double * 3)]
+
+    def as_dict(self):
+        return {f: (list(getattr(self, f)) if f.startswith("kind_") else getattr(self, f)) for f, _ in self._fields_}
+
+
 class CBatchInfo(ctypes.Structure):
     _fields_ = [("n_b", c_int32), ("ctas_per_sm", c_int32), ("rounds", c_int32), ("workers", c_int32),
                 ("n_width16", c_int32), ("n_width32", c_int32), ("n_width64", c_int32), ("reserved", c_int32),
@@ -115,6 +130,8 @@ def load(path: str = LIB_PATH):
     lib.polfed_ctx_destroy.argtypes = [c_void_p]
     lib.polfed_ctx_destroy.restype = None
     lib.polfed_ctx_set_stream.argtypes = [c_void_p, c_void_p]
+    lib.polfed_ctx_set_progress.argtypes = [c_void_p, PROGRESS_FN, c_void_p]
+    lib.polfed_get_counters.argtypes = [POINTER(CCounters)]
     lib.polfed_block_lanczos.argtypes = [c_void_p, POINTER(CModel), c_double, c_double, c_double, c_int32, c_int32,
                                          c_int32, c_void_p, POINTER(c_double), POINTER(c_double), POINTER(c_int32)]
     lib.polfed_eigs.argtypes = [c_void_p, POINTER(CModel), c_double, c_int32, c_int32, c_int32, POINTER(COpts),
@@ -266,6 +283,23 @@ class Ctx:
 
     def set_stream(self, stream):
         _check(self.lib.polfed_ctx_set_stream(self.h, _stream(stream)))
+
+    def set_progress(self, fn):
+        """polfed_ctx_set_progress: fn(phase, index) at every phase boundary (None removes it).
+        The ctypes thunk is kept on the context so that it outlives the calls."""
+        if fn is None:
+            self._progress = None
+            _check(self.lib.polfed_ctx_set_progress(self.h, PROGRESS_FN(), None))
+            return
+        self._progress = PROGRESS_FN(lambda user, phase, index: fn(int(phase), int(index)))
+        _check(self.lib.polfed_ctx_set_progress(self.h, self._progress, None))
+
+
+def get_counters() -> dict:
+    """polfed_get_counters: this thread's launch and step-kernel counters (monotone)."""
+    c = CCounters()
+    _check(load().polfed_get_counters(byref(c)))
+    return c.as_dict()
 
 
 def ctx_create(device=0, workspace_bytes=0) -> Ctx:

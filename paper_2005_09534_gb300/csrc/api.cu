@@ -19,6 +19,8 @@ int fail(int code, const std::string& msg) {
   return code;
 }
 
+void clear_error() { t_err.clear(); }
+
 static int check_block_args(const polfed_model* model, const uint32_t* d_states, int64_t dim, const void* X,
                             const void* Y, int n_b, int dtype) {
   if (!model) return fail(POLFED_EINVAL, "model is NULL");
@@ -58,6 +60,21 @@ using namespace polfed;
 extern "C" {
 
 const char* polfed_last_error(void) { return t_err.c_str(); }
+
+int polfed_get_counters(polfed_counters* out) {
+  if (!out) return fail(POLFED_EINVAL, "out is NULL");
+  const Counters& c = counters();
+  out->launches = c.launches;
+  out->step_launches = c.step_launches;
+  out->step_gpu_s = c.step_gpu_s;
+  out->step_alg_bytes = c.step_alg_bytes;
+  for (int k = 0; k < 3; k++) {
+    out->kind_launches[k] = c.kind_launches[k];
+    out->kind_gpu_s[k] = c.kind_gpu_s[k];
+    out->kind_alg_bytes[k] = c.kind_alg_bytes[k];
+  }
+  return POLFED_OK;
+}
 
 void polfed_opts_default(polfed_opts* o) {
   if (!o) return;

@@ -976,18 +976,29 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
         atomicExch(err, 1);
       }
       // every copy already issued must land before the CTA may exit: wait for
-      // the last phase of each buffer that received one (bounded)
+      // the last phase of each buffer that received one (bounded; a drain that
+      // runs out of polls is reported as a timeout, so the output is discarded)
+      bool drained = true;
       for (int sl = 0; sl < NS; sl++) {
         const int uses = q > sl ? (q - 1 - sl) / NS + 1 : 0;
-        if (uses > 0)
-          for (uint32_t i = 0; i < (1u << 22); ++i)
-            if (mbar_try_wait(&full[sl], (uint32_t)((uses - 1) & 1))) break;
+        if (uses > 0) {
+          bool landed = false;
+          for (uint32_t i = 0; i < (1u << 22) && !landed; ++i) landed = mbar_try_wait(&full[sl], (uint32_t)((uses - 1) & 1));
+          drained = drained && landed;
+        }
       }
       for (int b = 0; b < 2; b++) {
         const int uses = n_own > b ? (n_own - 1 - b) / 2 + 1 : 0;
-        if (uses > 0)
-          for (uint32_t i = 0; i < (1u << 22); ++i)
-            if (mbar_try_wait(&own_full[b], (uint32_t)((uses - 1) & 1))) break;
+        if (uses > 0) {
+          bool landed = false;
+          for (uint32_t i = 0; i < (1u << 22) && !landed; ++i)
+            landed = mbar_try_wait(&own_full[b], (uint32_t)((uses - 1) & 1));
+          drained = drained && landed;
+        }
+      }
+      if (!drained) {
+        s_abort = 1;
+        atomicExch(err, 1);
       }
     }
     return;
@@ -2314,6 +2325,7 @@ extern "C" int polfed_cheb_filter_static(const polfed_model* model, const uint32
                                          const void* d_X, void* d_Y, int32_t n_b, int32_t dtype,
                                          polfed_stream_t stream) {
   using namespace polfed;
+  clear_error();
   if (!model) return fail(POLFED_EINVAL, "model is NULL");
   if (model->L < 4 || model->L > 32 || (model->L & 1)) return fail(POLFED_EINVAL, "L must be even, 4 <= L <= 32");
   if (dim != (int64_t)binom_host(model->L, model->L / 2)) return fail(POLFED_EINVAL, "dim != C(L, L/2)");

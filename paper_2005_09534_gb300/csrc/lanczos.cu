@@ -87,6 +87,9 @@ struct polfed_ctx {
   DevBuf basis, U, R, fscr, ritz, small, evbuf, work, vecs, kpm;
   Dense dense;
   polfed_stats last;
+  polfed_progress_fn progress = nullptr;
+  void* progress_user = nullptr;
+  int block_steps = 0;  // block-Lanczos steps of the current run (over restarts), for the hook's index
 };
 
 namespace {
@@ -99,6 +102,13 @@ struct ScopedDevice {
   }
   ~ScopedDevice() { cudaSetDevice(prev); }
 };
+
+// Phase boundary: the stream is drained first so that the hook sees the step's work complete.
+void notify(polfed_ctx* c, int phase, int index) {
+  if (!c->progress) return;
+  cudaStreamSynchronize(c->stream);
+  c->progress(c->progress_user, phase, index);
+}
 
 // Symmetric eigen-solve of the n x n column-major matrix A (lda) on the
 // device with cuSOLVER (the projected problem); A is overwritten by the
@@ -272,6 +282,7 @@ int run_lanczos(polfed_ctx* c, HamPlan& plan, const LanczosParams& P, double* d_
   const double p = P.o.p;
   double tol_cur = P.o.tol_conv;
   std::vector<double> colnrm(S);
+  auto step_done = [&] { notify(c, POLFED_PHASE_BLOCK, c->block_steps++); };
   for (int j = 0; j < m_max; j++) {
     double* Qj = Qb + (int64_t)j * pstride;
     double t0 = now_s();
@@ -333,12 +344,16 @@ int run_lanczos(polfed_ctx* c, HamPlan& plan, const LanczosParams& P, double* d_
     m_done = j + 1;
     if (brk) {
       status = fail(POLFED_ENOCONV, "Lanczos breakdown (rank-deficient residual block)");
+      step_done();
       break;
     }
     // convergence check
     const int n = m_done * S;
     const bool last = (j == m_max - 1);
-    if (n < (int)((1.0 + P.o.k_margin) * P.N_ev) && !last) continue;
+    if (n < (int)((1.0 + P.o.k_margin) * P.N_ev) && !last) {
+      step_done();
+      continue;
+    }
     std::vector<double> T((size_t)n * n, 0.0);  // column-major, symmetric
     for (int i = 0; i < m_done; i++) {
       for (int a = 0; a < S; a++)
@@ -420,10 +435,12 @@ int run_lanczos(polfed_ctx* c, HamPlan& plan, const LanczosParams& P, double* d_
                 P.tol_resid_t);
       if (out.n_out >= P.N_ev && (mr <= P.tol_resid_t || P.accept_any)) {
         stopped = true;
+        step_done();
         break;
       }
       tol_cur = 0.1 * std::min(tol_cur, maxres_top);  // not accurate enough yet: demand smaller Ritz residuals
     }
+    step_done();
   }
   out.m = m_done;
   if (!stopped && status == POLFED_OK) status = fail(POLFED_ENOCONV, "column budget exhausted before convergence");
@@ -848,6 +865,7 @@ int polfed_block_lanczos(polfed_ctx* c, const polfed_model* model, double e_lo, 
                   false, false};
   LanczosOut o;
   const double t0 = now_s();
+  c->block_steps = 0;
   int rc = run_lanczos(c, plan, P, d_evecs, o);
   if (rc != POLFED_OK && rc != POLFED_ENOCONV) return rc;
   const double half = 0.5 * (e_hi - e_lo), mid = 0.5 * (e_hi + e_lo);
@@ -876,7 +894,15 @@ int polfed_block_lanczos(polfed_ctx* c, const polfed_model* model, double e_lo, 
   st.t_total = now_s() - t0;
   st.status = rc;
   for (int i = 0; i < o.n_out; i++) st.max_resid = std::max(st.max_resid, o.resid_t[i] * half);
+  notify(c, POLFED_PHASE_END, rc);
   return rc;
+}
+
+int polfed_ctx_set_progress(polfed_ctx* c, polfed_progress_fn fn, void* user) {
+  if (!c) return fail(POLFED_EINVAL, "ctx is NULL");
+  c->progress = fn;
+  c->progress_user = user;
+  return POLFED_OK;
 }
 
 int polfed_eigs(polfed_ctx* c, const polfed_model* model, double eps_target, int32_t N_ev, int32_t K, int32_t n_b,
@@ -997,6 +1023,8 @@ int eigs_impl(polfed_ctx* c, const polfed_model* model, double eps_target, int32
     fprintf(stderr, "[polfed] dim %lld  E_min %.12f  E_max %.12f (err %.1e)  sigma %.3e  mean %.4f  Gamma %.4f  rho~ %.4e  K %d\n",
             (long long)dim, Emin, Emax, berr, sigma, mean, gam, rho_t, K);
   // 3. block Lanczos
+  c->block_steps = 0;
+  notify(c, POLFED_PHASE_START, K);
   const int S = round_block(n_b);
   const double hnorm0 = std::max(std::fabs(Emin), std::fabs(Emax));
   const bool mixed = o.precision == POLFED_F32;
@@ -1051,6 +1079,7 @@ int eigs_impl(polfed_ctx* c, const polfed_model* model, double eps_target, int32
       const int rrc = refine(c, plan, P, Kr, lo.ritz_cols, d_evecs, lo);
       lo.t_ritz += now_s() - tr0;
       if (rrc != POLFED_OK) return rrc;
+      notify(c, POLFED_PHASE_REFINE, sweep);
       lo.n_refine++;
       lo.refine_K = Kr;
       Kr = std::min(2 * Kr, K);
@@ -1138,6 +1167,7 @@ int eigs_impl(polfed_ctx* c, const polfed_model* model, double eps_target, int32
   if (stats) *stats = st;
   if (rc == POLFED_OK && st.max_resid > o.tol_resid * hnorm && o.verbose)
     fprintf(stderr, "[polfed] warning: max residual %.3e exceeds tol %.3e\n", st.max_resid, o.tol_resid * hnorm);
+  notify(c, POLFED_PHASE_END, rc);
   return rc;
 }
 

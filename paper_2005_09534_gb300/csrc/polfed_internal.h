@@ -18,6 +18,7 @@ struct Error {
 };
 void set_error(int code, const std::string& msg);
 int fail(int code, const std::string& msg);  // set_error + return code
+void clear_error();                          // an entry point starts with an empty message
 
 #define PF_CUDA(call)                                                                          \
   do {                                                                                         \

@@ -4,14 +4,17 @@ import json
 import os
 import subprocess
 import sys
+import time
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def test_reference_arm_json_line():
     env = dict(os.environ, OMP_NUM_THREADS="2", OPENBLAS_NUM_THREADS="2")
-    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+    t0 = time.perf_counter()
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "2",
                           "--warmup", "3"], capture_output=True, text=True, timeout=600, env=env, cwd=ROOT)
+    wall = time.perf_counter() - t0
     assert out.returncode == 0, out.stderr
     lines = [l for l in out.stdout.splitlines() if l.strip()]
     assert len(lines) == 1
@@ -22,3 +25,8 @@ def test_reference_arm_json_line():
     assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] == "eigenpairs/s"
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+    # the per-step time is what the timed steps actually took: it fits the process's wall time
+    assert 0 < d["ms_per_step"] * d["steps"] / 1e3 < wall
+    cb = d["cpu_baseline"]
+    assert cb["seconds_per_cheb_step"] > 0 and cb["extrapolated_run_s"] > d["ms_per_step"] / 1e3
+    assert d["config"]["K"] > 1000 and d["config"]["m"] >= 2 * d["config"]["N_ev"] / d["config"]["n_b"]

@@ -31,7 +31,8 @@ def _rank_main(rank, world, port, out_dir):
     dist.init_process_group("gloo", rank=rank, world_size=world)
     cpu = torch.device("cpu")
     # rank r reports device time 1 + r, wall time 2 + r and 10 + r passing eigenpairs
-    t_dev, wall, pairs = bench.reduce_ranks(torch, cpu, dist, 1.0 + rank, 2.0 + rank, 10 + rank)
+    t_dev, wall, pairs, pairs_wall = bench.reduce_ranks(torch, cpu, dist, 1.0 + rank, 2.0 + rank, 10 + rank,
+                                                         7.5 + rank)
     mine = [bench.timed_realization(k, world, rank) for k in range(5)]
     mine += [bench.warmup_realization(w, world, rank) for w in range(3)]
     gathered = [None] * world
@@ -43,7 +44,7 @@ def _rank_main(rank, world, port, out_dir):
     dist.all_gather_object(all_seeds, seeds)
     dist.destroy_process_group()
     with open(os.path.join(out_dir, f"rank{rank}.txt"), "w") as f:
-        f.write(repr((t_dev, wall, pairs, gathered, [len(set(x)) for x in all_seeds],
+        f.write(repr((t_dev, wall, pairs, pairs_wall, gathered, [len(set(x)) for x in all_seeds],
                       len(set(all_seeds[0]) & set(all_seeds[1])))))
 
 
@@ -53,8 +54,19 @@ def test_two_gloo_ranks_reduce_and_shard(tmp_path):
     port = _free_port()
     mp.start_processes(_rank_main, args=(2, port, str(tmp_path)), nprocs=2, join=True, start_method="spawn")
     res = [eval(open(tmp_path / f"rank{r}.txt").read()) for r in range(2)]
-    for t_dev, wall, pairs, gathered, n_unique, n_shared in res:
-        assert (t_dev, wall, pairs) == (2.0, 3.0, 21)  # max, max, sum
+    for t_dev, wall, pairs, pairs_wall, gathered, n_unique, n_shared in res:
+        assert (t_dev, wall, pairs, pairs_wall) == (2.0, 3.0, 21.0, 16.0)  # max, max, sum, sum
         a, b = set(gathered[0]), set(gathered[1])
         assert len(a) == len(gathered[0]) and not (a & b)  # disjoint realizations
         assert n_unique == [128, 128] and n_shared == 0  # batched workloads: distinct field sets per rank
+
+
+def test_credited_pairs_by_overlap():
+    import bench
+    runs = [(0.0, 10.0, 100), (10.0, 20.0, 50), (20.0, 40.0, 80)]
+    # half of run 0, half of run 1, none of run 2
+    assert abs(bench.credited_pairs(runs, 5.0, 15.0) - 75.0) < 1e-12
+    # all of run 1 and a quarter of run 2
+    assert abs(bench.credited_pairs(runs, 10.0, 25.0) - 70.0) < 1e-12
+    # one run at a constant rate: the credited rate equals the run's rate
+    assert abs(bench.credited_pairs([(0.0, 8.0, 40)], 2.0, 6.0) / 4.0 - 5.0) < 1e-12

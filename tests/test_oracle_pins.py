@@ -297,3 +297,78 @@ def test_input_generator_is_deterministic():
     assert not np.array_equal(a, I.fields(22, 3.0, 4, 2))
     # splitmix64 reference values for seed 0 (published test vector of the generator)
     assert I.splitmix64_stream(0, 3) == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+# ------------------------------------------------- order selection ("POLFED algorithm")
+
+def test_sector_moments_match_the_spectrum():
+    # traces give the spectrum's mean and variance without an eigen-solve
+    m = I.j1j2(10, 3.0, 2, 0)
+    H, _ = O.dense_hamiltonian(m.L, m.J1, m.J2, m.Delta, m.h, True)
+    w = np.linalg.eigvalsh(H)
+    mean, var = O.sector_moments(H)
+    assert abs(mean - w.mean()) < 1e-12 and abs(var - w.var()) < 1e-11
+    Hs, _ = O.sparse_hamiltonian(m.L, m.J1, m.J2, m.Delta, m.h, True)
+    ms, vs = O.sector_moments(Hs)
+    assert abs(ms - mean) < 1e-12 and abs(vs - var) < 1e-11
+
+
+def test_gaussian_rho_normalization():
+    # a density of states integrates to the number of states
+    x = np.linspace(-40.0, 40.0, 400001)
+    r = np.array([O.gaussian_rho(1000, 1.5, 9.0, e) for e in x[::100]])
+    assert abs(np.trapezoid(r, x[::100]) - 1000.0) < 1e-6
+
+
+@pytest.mark.parametrize("rho_t,n_target", [(2.0e4, 60.0), (5.0e4, 120.0), (3.0e5, 600.0)])
+def test_order_for_window_fills_the_main_lobe(rho_t, n_target):
+    # the chosen even K holds n_target values in its lobe; K + 2 no longer does.
+    # The lobe is measured by scanning P itself (lobe_halfwidth), not by the
+    # Dirichlet closed form that order_for_window uses.
+    K = O.order_for_window(rho_t, n_target)
+    assert K % 2 == 0
+    assert O.n_accessible(rho_t, 0.0, K) >= n_target * (1 - 1e-9)
+    assert O.n_accessible(rho_t, 0.0, K + 2) < n_target
+    # large-K limit: K + 1 -> 2 y* rho / n_target with sin(y*)/y* = p
+    assert abs((K + 1) / (2 * 2.6704 * rho_t / n_target) - 1.0) < 2.0 / (K + 1) + 2e-4
+
+
+def test_order_for_window_counts_a_real_window():
+    # L = 14 XXZ ring, W = 3: with the Gaussian density of the exact moments,
+    # the window of the chosen K holds about the requested number of eigenvalues
+    m = I.xxz(14, 3.0, 1, 0)
+    H, _ = O.dense_hamiltonian(m.L, m.J1, m.J2, m.Delta, m.h, True)
+    w = np.linalg.eigvalsh(H)
+    lo, hi = w[0], w[-1]
+    mean, var = O.sector_moments(H)
+    Es = 0.5 * (lo + hi)
+    rho_t = O.gaussian_rho(len(w), mean, var, Es) * 0.5 * (hi - lo)
+    K = O.order_for_window(rho_t, 60.0)
+    lt = (2 * w - lo - hi) / (hi - lo)
+    n_in = int(np.sum(O.P_scalar(lt, 0.0, K) >= O.P_THRESHOLD))
+    assert 40 <= n_in <= 80, (K, n_in)
+
+
+def test_extreme_eigenvalues_match_dense():
+    m = I.j1j2(12, 4.0, 2, 1)
+    Hs, _ = O.sparse_hamiltonian(m.L, m.J1, m.J2, m.Delta, m.h, True)
+    H, _ = O.dense_hamiltonian(m.L, m.J1, m.J2, m.Delta, m.h, True)
+    w = np.linalg.eigvalsh(H)
+    lo, hi = O.extreme_eigenvalues(Hs)
+    assert abs(lo - w[0]) < 1e-9 and abs(hi - w[-1]) < 1e-9
+
+
+def test_residual_norms_two_level_closed_form():
+    # u = cos(t) v_i + sin(t) v_j with eigenvectors v_i, v_j: the Rayleigh value is
+    # e = cos^2 l_i + sin^2 l_j and ||H u - e u|| = |sin t cos t| |l_i - l_j|
+    m = I.xxz(8, 2.0, 1, 3)
+    H, _ = O.dense_hamiltonian(m.L, m.J1, m.J2, m.Delta, m.h, True)
+    w, V = np.linalg.eigh(H)
+    i, j = 3, 17
+    us, es, want = [], [], []
+    for t in (0.0, 0.1, 0.7):
+        us.append(math.cos(t) * V[:, i] + math.sin(t) * V[:, j])
+        es.append(math.cos(t) ** 2 * w[i] + math.sin(t) ** 2 * w[j])
+        want.append(abs(math.sin(t) * math.cos(t)) * abs(w[i] - w[j]))
+    got = O.residual_norms(H, np.array(es), np.stack(us, axis=1))
+    assert np.allclose(got, want, atol=1e-12)
