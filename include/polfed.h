@@ -84,6 +84,10 @@ typedef struct polfed_opts {
                             Lanczos probe confirms that they contain the spectrum, else ignored (0, 0 = none) */
   int32_t kpm_moments;   /* POLFED_DOS_KPM: Chebyshev moments (default 256) */
   int32_t kpm_vectors;   /* POLFED_DOS_KPM: random vectors of the stochastic trace (default 16) */
+  double tol_refine;     /* POLFED_F32: refinement sweeps continue (at most 6) until every residual is
+                            <= tol_refine * ||H||; 0 = tol_resid.  Eigenvector-derived quantities such as the
+                            entanglement entropy move with the eigenvector error ~ residual / level spacing, so
+                            a smaller value buys them accuracy; acceptance still uses tol_resid */
 } polfed_opts;
 
 /* Density-of-states rules for the choice of K (polfed_opts.dos_rule). */
@@ -131,7 +135,7 @@ typedef struct polfed_ctx polfed_ctx;
 
 /* Default options: p = 0.17, k_margin = 0.2, tol_conv = 1e-7 (tightened until the residuals pass), tol_resid = 1e-8,
  * cols_factor = 2.8, precision = POLFED_DF64, bounds_steps = 600, dos_rule = POLFED_DOS_MOMENTS, seed = 1234,
- * no hints, kpm_moments = 256, kpm_vectors = 16. */
+ * no hints, kpm_moments = 256, kpm_vectors = 16, tol_refine = 0. */
 void polfed_opts_default(polfed_opts* opts);
 
 /* Basis of the S^z sector with n_up up spins ("Benchmark models": N = C(L, L/2)
@@ -230,6 +234,25 @@ enum {
  * fn = NULL removes the hook.  Not used by the batched runner. */
 typedef void (*polfed_progress_fn)(void* user, int32_t phase, int32_t index);
 int polfed_ctx_set_progress(polfed_ctx* ctx, polfed_progress_fn fn, void* user);
+
+/* One convergence check of block Lanczos (the eigen-solve of T_j and the test
+ * ||B_{j+1} t~_i|| after Eq. (4); the Supplement's "Convergence of POLFED"
+ * follows the converged count against the number of Lanczos columns). */
+typedef struct polfed_conv_point {
+  int32_t step;        /* block-Lanczos step j (1-based) of the attempt */
+  int32_t cols;        /* Lanczos columns m s at the check */
+  int32_t n_conv;      /* Ritz values theta >= p whose ||B t~|| <= the current tolerance */
+  int32_t n_acc;       /* Ritz values theta >= p */
+  int32_t attempt;     /* 0 = first run; restarts with a smaller K and the float-float rerun count up */
+  int32_t reserved;
+  double theta_nev;    /* N_ev-th largest Ritz value (-1 if fewer columns) */
+  double max_res_top;  /* largest ||B t~|| among the N_ev largest Ritz values */
+} polfed_conv_point;
+
+/* Convergence history of the last polfed_eigs / polfed_block_lanczos call on
+ * ctx: copies min(max, available) checks to out (host) and sets *n to the
+ * number available. */
+int polfed_ctx_history(polfed_ctx* ctx, polfed_conv_point* out, int32_t max, int32_t* n);
 
 /* Process counters of this library's device work issued by the calling host
  * thread since it first called the library (monotone; take differences):
@@ -446,6 +469,48 @@ int polfed_eigs_batched(int32_t device, int32_t n_inst, const polfed_model* mode
                         const int32_t* N_ev, const int32_t* K, int32_t n_b, const polfed_opts* opts,
                         int32_t max_workers, double* evals, double* resid, double* const* d_evecs,
                         polfed_stats* stats, int32_t* status, polfed_batch_info* info);
+
+/* Test support for the failure path (the paper has no counterpart).  Every
+ * device-side wait of this library is bounded: the bulk-copy pipeline of the
+ * step kernel polls its mbarriers at most 2^22 times, the grid barrier of the
+ * batched filter at most 2^24 times (about a second); a wait that runs out
+ * makes the kernel stop, wait with the full cap for the copies it already
+ * issued, and the call returns POLFED_ETIMEOUT with its output discarded.
+ * polfed_set_wait_limit(polls) lowers both caps to `polls` for the calls that
+ * follow in this process (0 restores the defaults), so a test can make the
+ * waits run out without stalling anything.  Not for production use. */
+int polfed_set_wait_limit(uint32_t polls);
+
+/* ------------------------------------------------------------------------
+ * Observables of the eigenpairs (section "Entanglement entropy and level
+ * statistics").
+ * ------------------------------------------------------------------------ */
+
+/* Mean gap ratio r = (1 / (n - 2)) sum_i min(g_i, g_{i+1}) / max(g_i, g_{i+1}),
+ * g_i = E_{i+1} - E_i (the level-statistics indicator of that section).
+ *   d_evals : device, n eigenvalues in ascending order (e.g. polfed_eigs' evals copied over).
+ *   n       : >= 3.
+ *   r_mean  : host out.
+ *   d_r     : device out, the n - 2 ratios r_i, or NULL.
+ * Synchronizes the stream.  POLFED_EINVAL if the values are not ascending or
+ * two consecutive gaps are both zero (the ratio is undefined). */
+int polfed_gap_ratio(const double* d_evals, int32_t n, double* r_mean, double* d_r, polfed_stream_t stream);
+
+/* Half-chain entanglement entropy S_E = -sum alpha^2 ln alpha^2 of S^z = 0
+ * sector vectors for the cuts A = [x, x + L/2) (sites mod L) of that section,
+ * from the Schmidt coefficients alpha (per block of fixed magnetization of A,
+ * the eigenvalues of M_k M_k^T, natural logarithm).
+ *   ctx      : context (device, stream, cuSOLVER handle).
+ *   L        : even, 4 <= L <= 32.
+ *   d_states : device basis from polfed_basis_build(L, L/2).
+ *   d_vecs   : device, column-major dim x n_vec FP64 (vector v at d_vecs + v * ld), normalized
+ *              (e.g. polfed_eigs' d_evecs).
+ *   per_cut  : 0 = S[v] is the average over the L cut positions x = 0..L-1;
+ *              1 = S[v * L + x] is the entropy of cut x.
+ *   S        : host out.
+ * Uses stream-ordered device scratch of about 2 GiB at most.  Blocking. */
+int polfed_entanglement_entropy(polfed_ctx* ctx, int32_t L, const uint32_t* d_states, const double* d_vecs,
+                                int64_t ld, int32_t n_vec, int32_t per_cut, double* S);
 
 /* Message of the last failing call on this thread ("" if none). */
 const char* polfed_last_error(void);

@@ -506,12 +506,15 @@ def entanglement_entropy_cut(vec: np.ndarray, states: np.ndarray, L: int, x: int
     half = L // 2
     A = [(x + k) % L for k in range(half)]
     B = [s for s in range(L) if s not in A]
+    states = np.asarray(states, dtype=np.int64)
+    a = np.zeros(len(states), dtype=np.int64)  # index of each state's configuration of A
+    b = np.zeros(len(states), dtype=np.int64)  # and of B
+    for k, site in enumerate(A):
+        a |= ((states >> site) & 1) << k
+    for k, site in enumerate(B):
+        b |= ((states >> site) & 1) << k
     M = np.zeros((1 << half, 1 << (L - half)))
-    for amp, s in zip(vec, states):
-        s = int(s)
-        a = sum(((s >> site) & 1) << k for k, site in enumerate(A))
-        b = sum(((s >> site) & 1) << k for k, site in enumerate(B))
-        M[a, b] += amp
+    np.add.at(M, (a, b), np.asarray(vec, dtype=np.float64))
     sv = np.linalg.svd(M, compute_uv=False)
     a2 = sv ** 2
     a2 = a2[a2 > 1e-300]

@@ -37,12 +37,13 @@ PROGRESS_FN = ctypes.CFUNCTYPE(None, c_void_p, c_int32, c_int32)
 EXPORTED = ["polfed_opts_default", "polfed_basis_build", "polfed_h_apply", "polfed_cheb_filter",
             "polfed_cheb_filter_static",
             "polfed_ctx_create", "polfed_ctx_destroy", "polfed_ctx_set_stream", "polfed_ctx_set_progress",
-            "polfed_get_counters", "polfed_block_lanczos",
+            "polfed_get_counters", "polfed_ctx_history", "polfed_block_lanczos",
             "polfed_eigs", "polfed_spectral_bounds", "polfed_kpm_moments", "polfed_kpm_count",
             "polfed_spectral_labels", "polfed_mlp_create", "polfed_mlp_destroy", "polfed_mlp_num_params",
             "polfed_mlp_set_params", "polfed_mlp_get_params", "polfed_mlp_set_scaling", "polfed_mlp_forward",
             "polfed_mlp_grad", "polfed_mlp_train_step", "polfed_mlp_features", "polfed_mlp_targets",
-            "polfed_mlp_predict", "polfed_cheb_filter_batched", "polfed_eigs_batched", "polfed_last_error"]
+            "polfed_mlp_predict", "polfed_cheb_filter_batched", "polfed_eigs_batched", "polfed_gap_ratio",
+            "polfed_entanglement_entropy", "polfed_set_wait_limit", "polfed_last_error"]
 
 
 class PolfedError(RuntimeError):
@@ -61,7 +62,7 @@ class COpts(ctypes.Structure):
                 ("cols_factor", c_double), ("precision", c_int32), ("bounds_steps", c_int32),
                 ("verbose", c_int32), ("dos_rule", c_int32), ("seed", c_uint64), ("rho_hint", c_double),
                 ("emin_hint", c_double), ("emax_hint", c_double), ("kpm_moments", c_int32),
-                ("kpm_vectors", c_int32)]
+                ("kpm_vectors", c_int32), ("tol_refine", c_double)]
 
 
 class CStats(ctypes.Structure):
@@ -92,6 +93,11 @@ class CCounters(ctypes.Structure):
 
     def as_dict(self):
         return {f: (list(getattr(self, f)) if f.startswith("kind_") else getattr(self, f)) for f, _ in self._fields_}
+
+
+class CConvPoint(ctypes.Structure):
+    _fields_ = [("step", c_int32), ("cols", c_int32), ("n_conv", c_int32), ("n_acc", c_int32),
+                ("attempt", c_int32), ("reserved", c_int32), ("theta_nev", c_double), ("max_res_top", c_double)]
 
 
 class CBatchInfo(ctypes.Structure):
@@ -132,6 +138,7 @@ def load(path: str = LIB_PATH):
     lib.polfed_ctx_set_stream.argtypes = [c_void_p, c_void_p]
     lib.polfed_ctx_set_progress.argtypes = [c_void_p, PROGRESS_FN, c_void_p]
     lib.polfed_get_counters.argtypes = [POINTER(CCounters)]
+    lib.polfed_ctx_history.argtypes = [c_void_p, POINTER(CConvPoint), c_int32, POINTER(c_int32)]
     lib.polfed_block_lanczos.argtypes = [c_void_p, POINTER(CModel), c_double, c_double, c_double, c_int32, c_int32,
                                          c_int32, c_void_p, POINTER(c_double), POINTER(c_double), POINTER(c_int32)]
     lib.polfed_eigs.argtypes = [c_void_p, POINTER(CModel), c_double, c_int32, c_int32, c_int32, POINTER(COpts),
@@ -161,6 +168,10 @@ def load(path: str = LIB_PATH):
                                         POINTER(c_int32), c_int32, POINTER(COpts), c_int32, POINTER(c_double),
                                         POINTER(c_double), POINTER(c_void_p), POINTER(CStats), POINTER(c_int32),
                                         POINTER(CBatchInfo)]
+    lib.polfed_set_wait_limit.argtypes = [ctypes.c_uint32]
+    lib.polfed_gap_ratio.argtypes = [c_void_p, c_int32, POINTER(c_double), c_void_p, c_void_p]
+    lib.polfed_entanglement_entropy.argtypes = [c_void_p, c_int32, c_void_p, c_void_p, c_int64, c_int32, c_int32,
+                                                POINTER(c_double)]
     for name in EXPORTED:
         getattr(lib, name)
     _lib = lib
@@ -293,6 +304,15 @@ class Ctx:
             return
         self._progress = PROGRESS_FN(lambda user, phase, index: fn(int(phase), int(index)))
         _check(self.lib.polfed_ctx_set_progress(self.h, self._progress, None))
+
+
+def history(ctx) -> list:
+    """polfed_ctx_history: the convergence checks of the last call on ctx, as dicts."""
+    n = c_int32(0)
+    _check(load().polfed_ctx_history(ctx.h, None, 0, byref(n)))
+    arr = (CConvPoint * max(1, n.value))()
+    _check(load().polfed_ctx_history(ctx.h, arr, n.value, byref(n)))
+    return [{f: getattr(arr[i], f) for f, _ in CConvPoint._fields_ if f != "reserved"} for i in range(n.value)]
 
 
 def get_counters() -> dict:
@@ -496,3 +516,24 @@ def eigs_batched(models, eps_target, N_ev, K=None, n_b=0, opts=None, max_workers
     evs = [ev[offs[i]:offs[i + 1]] for i in range(n)]
     res = [rs[offs[i]:offs[i + 1]] for i in range(n)]
     return evs, res, [s.as_dict() for s in st], status, info.as_dict(), rc
+
+
+def gap_ratio(d_evals, n, d_r=None, stream=None) -> float:
+    """polfed_gap_ratio: mean gap ratio of n ascending eigenvalues on the device."""
+    r = c_double(0.0)
+    _check(load().polfed_gap_ratio(_ptr(d_evals), int(n), byref(r), _ptr(d_r), _stream(stream)))
+    return r.value
+
+
+def entanglement_entropy(ctx, L, d_states, d_vecs, ld, n_vec, per_cut=False):
+    """polfed_entanglement_entropy: numpy array of n_vec cut-averaged entropies, or
+    n_vec x L per-cut entropies with per_cut."""
+    out = np.zeros(int(n_vec) * (int(L) if per_cut else 1))
+    _check(load().polfed_entanglement_entropy(ctx.h, int(L), _ptr(d_states), _ptr(d_vecs), int(ld), int(n_vec),
+                                              1 if per_cut else 0, _dptr(out)))
+    return out.reshape(int(n_vec), int(L)) if per_cut else out
+
+
+def set_wait_limit(polls: int):
+    """polfed_set_wait_limit: cap every bounded device wait at `polls` iterations (0 = defaults); tests only."""
+    _check(load().polfed_set_wait_limit(int(polls)))

@@ -93,6 +93,7 @@ void polfed_opts_default(polfed_opts* o) {
   o->emax_hint = 0.0;
   o->kpm_moments = 256;
   o->kpm_vectors = 16;
+  o->tol_refine = 0.0;
 }
 
 int polfed_basis_build(int32_t L, int32_t n_up, uint32_t* d_states, int64_t* dim, polfed_stream_t stream) {

@@ -27,6 +27,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 #include <type_traits>
 
@@ -674,6 +675,19 @@ __global__ void __launch_bounds__(256, 2) k_ham_step(const HamGeometry g, const 
                                    sCx);
 }
 
+// -------------------------------------------------------- bounded waits
+// Iteration caps of the device-side waits: the TMA pipeline's mbarrier waits
+// and the batched kernel's grid barrier.  A wait that runs out makes the
+// kernel stop, drain the copies it issued (always with the full cap) and
+// report POLFED_ETIMEOUT.  polfed_set_wait_limit lowers the caps for tests.
+constexpr uint32_t kMbarWaitPolls = 1u << 22;
+constexpr uint32_t kBarrierWaitPolls = 1u << 24;
+static std::atomic<uint32_t> g_wait_limit{0};
+static uint32_t wait_cap(uint32_t dflt) {
+  const uint32_t v = g_wait_limit.load();
+  return v == 0 ? dflt : std::min(v, dflt);
+}
+
 // ------------------------------------------------ batched persistent filter
 // Many independent filter jobs -- one 128-byte column slice of one disorder
 // realization each, with its own operator tables, order K and coefficients --
@@ -693,7 +707,7 @@ struct BatchJob {
   int cross_lo[6], cross_cls[6];
 };
 
-__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, int* err) {
+__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, int* err, uint32_t cap) {
   __syncthreads();
   int ok = 1;
   if (threadIdx.x == 0) {
@@ -711,7 +725,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, int
           ok = 0;
           break;
         }
-        if (++it > (1u << 24)) {  // about a second of 32-64 ns naps
+        if (++it > cap) {  // default 2^24: about a second of 32-64 ns naps
           atomicExch(err, 1);
           ok = 0;
           break;
@@ -756,7 +770,7 @@ __device__ __forceinline__ void make_kc(double cX, double cH, double cB, double 
 template <class NT, bool J2>
 __global__ void __launch_bounds__(256, 2)
     k_filter_batched(const BatchJob* __restrict__ jobs, int n_jobs, int n_steps, int tile_elems, int nlo_max,
-                     unsigned* bar_count, unsigned* bar_gen, int* err) {
+                     unsigned* bar_count, unsigned* bar_gen, int* err, uint32_t wait_cap) {
   using S = typename NT::S;
   using C = typename NT::C;
   constexpr int LPR = 8;
@@ -811,7 +825,7 @@ __global__ void __launch_bounds__(256, 2)
       }
       base += ng;
     }
-    if (!grid_barrier(bar_count, bar_gen, err)) return;
+    if (!grid_barrier(bar_count, bar_gen, err, wait_cap)) return;
   }
 }
 
@@ -847,8 +861,8 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* b, uint32_t parity) {
 }
 // Bounded wait: false if the phase did not complete within the iteration cap
 // or another thread already gave up.
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag) {
-  for (uint32_t it = 0; it < (1u << 22); ++it) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag, uint32_t cap) {
+  for (uint32_t it = 0; it < cap; ++it) {
     if (mbar_try_wait(b, parity)) return true;
     if (*abort_flag) return false;
   }
@@ -864,7 +878,7 @@ template <class NT, bool J2>
 __global__ void __launch_bounds__(kTmaThreads, 1)
     k_ham_step_tma(const HamGeometry g, const StepTables t, const typename NT::S* __restrict__ b1,
                    const typename NT::S* b2, const typename NT::S* __restrict__ x, typename NT::S* out,
-                   const typename NT::KC kc, int has_x, int has_b2, int* err) {
+                   const typename NT::KC kc, int has_x, int has_b2, int* err, uint32_t wait_cap) {
   using S = typename NT::S;
   using C = typename NT::C;
   using A = typename NT::A;
@@ -926,7 +940,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
       for (int ord = 0; ord < n_my && ok; ord++) {
         const GroupRec* G = t.grec + (int)blockIdx.x + ord * (int)gridDim.x;
         const int r0 = G->r0, n_g = G->n_g;
-        if (ord >= 2 && !mbar_wait(&own_empty[ord & 1], (uint32_t)(((ord >> 1) - 1) & 1), &s_abort)) {
+        if (ord >= 2 && !mbar_wait(&own_empty[ord & 1], (uint32_t)(((ord >> 1) - 1) & 1), &s_abort, wait_cap)) {
           ok = false;
           break;
         }
@@ -961,7 +975,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
           }
           if (!src) continue;
           const int slot = q % NS;
-          if (q >= NS && !mbar_wait(&empty[slot], (uint32_t)(((q / NS) - 1) & 1), &s_abort)) {
+          if (q >= NS && !mbar_wait(&empty[slot], (uint32_t)(((q / NS) - 1) & 1), &s_abort, wait_cap)) {
             ok = false;
             break;
           }
@@ -983,7 +997,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
         const int uses = q > sl ? (q - 1 - sl) / NS + 1 : 0;
         if (uses > 0) {
           bool landed = false;
-          for (uint32_t i = 0; i < (1u << 22) && !landed; ++i) landed = mbar_try_wait(&full[sl], (uint32_t)((uses - 1) & 1));
+          for (uint32_t i = 0; i < kMbarWaitPolls && !landed; ++i) landed = mbar_try_wait(&full[sl], (uint32_t)((uses - 1) & 1));
           drained = drained && landed;
         }
       }
@@ -991,7 +1005,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
         const int uses = n_own > b ? (n_own - 1 - b) / 2 + 1 : 0;
         if (uses > 0) {
           bool landed = false;
-          for (uint32_t i = 0; i < (1u << 22) && !landed; ++i)
+          for (uint32_t i = 0; i < kMbarWaitPolls && !landed; ++i)
             landed = mbar_try_wait(&own_full[b], (uint32_t)((uses - 1) & 1));
           drained = drained && landed;
         }
@@ -1034,7 +1048,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
     const int gidx = (int)blockIdx.x + ord * (int)gridDim.x;
     const C fhi = fhi_next;
     if (ord + 1 < n_my) fhi_next = gFhi[gidx + (int)gridDim.x];
-    if (!mbar_wait(&own_full[ord & 1], (uint32_t)((ord >> 1) & 1), &s_abort)) s_abort = 1;
+    if (!mbar_wait(&own_full[ord & 1], (uint32_t)((ord >> 1) & 1), &s_abort, wait_cap)) s_abort = 1;
     if (s_abort) break;
     const GroupRec* G = &s_grp[ord & 1];
     const int r0 = G->r0, n_g = G->n_g, cls_base = G->cls_base;
@@ -1108,7 +1122,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
     for (int k = 0; k < MAXCR; k++) {
       if (!(k < g.n_cross && G->cr_n[k] > 0)) continue;
       const int slot = q % NS;
-      if (!mbar_wait(&full[slot], (uint32_t)((q / NS) & 1), &s_abort)) s_abort = 1;
+      if (!mbar_wait(&full[slot], (uint32_t)((q / NS) & 1), &s_abort, wait_cap)) s_abort = 1;
       if (s_abort) break;
       const S* blk = ring + (size_t)slot * stg;
       const bool c1 = !J2 || !cr_c2[k];
@@ -1127,7 +1141,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
     if (s_abort) break;
     for (int k = 0; k < n_hn; k++) {
       const int slot = q % NS;
-      if (!mbar_wait(&full[slot], (uint32_t)((q / NS) & 1), &s_abort)) s_abort = 1;
+      if (!mbar_wait(&full[slot], (uint32_t)((q / NS) & 1), &s_abort, wait_cap)) s_abort = 1;
       if (s_abort) break;
       const S* blk = ring + (size_t)slot * stg;
       const bool c1 = !J2 || k < n_hn1;
@@ -1143,12 +1157,12 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
     if (s_abort) break;
     if (has_x) {
       x_slot = q % NS;
-      if (!mbar_wait(&full[x_slot], (uint32_t)((q / NS) & 1), &s_abort)) s_abort = 1;
+      if (!mbar_wait(&full[x_slot], (uint32_t)((q / NS) & 1), &s_abort, wait_cap)) s_abort = 1;
       q++;
     }
     if (has_b2 && !s_abort) {
       b2_slot = q % NS;
-      if (!mbar_wait(&full[b2_slot], (uint32_t)((q / NS) & 1), &s_abort)) s_abort = 1;
+      if (!mbar_wait(&full[b2_slot], (uint32_t)((q / NS) & 1), &s_abort, wait_cap)) s_abort = 1;
       q++;
     }
     if (s_abort) break;
@@ -1609,7 +1623,8 @@ static int launch_step_tma(const HamPlan& p, const StepArgs& a, cudaStream_t s) 
     kc.o2 = (C)o2;
   }
   kern<<<grid, kTmaThreads, smem, s>>>(g, t, (const S*)a.b1, (const S*)a.b2, (const S*)a.x, (S*)a.out, kc,
-                                       a.cX != 0.0 && a.x != nullptr, a.cB != 0.0 && a.b2 != nullptr, p.err_flag);
+                                       a.cX != 0.0 && a.x != nullptr, a.cB != 0.0 && a.b2 != nullptr, p.err_flag,
+                                       wait_cap(kMbarWaitPolls));
   PF_CUDA(cudaGetLastError());
   count_step(kk, (double)g.dim * 128.0 * (3.0 + (a.cX != 0.0 ? 1.0 : 0.0)));
   return POLFED_OK;
@@ -1890,8 +1905,9 @@ int launch_batched(const BatchJob* d_jobs, int n_jobs, int n_steps, int tile_ele
   int grid = nsm * per_sm;  // every CTA co-resident: the grid barrier cannot deadlock
   unsigned* count = bar;
   unsigned* gen = bar + 1;
+  uint32_t cap = wait_cap(kBarrierWaitPolls);
   void* args[] = {(void*)&d_jobs, (void*)&n_jobs, (void*)&n_steps, (void*)&tile_elems, (void*)&nlo_max,
-                  (void*)&count, (void*)&gen, (void*)&err};
+                  (void*)&count, (void*)&gen, (void*)&err, (void*)&cap};
   PF_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(256), args, smem, s));
   *grid_out = grid;
   return POLFED_OK;
@@ -2319,6 +2335,11 @@ static int static_filter(const polfed_model* model, double e_lo, double e_hi, co
 }
 
 }  // namespace polfed
+
+extern "C" int polfed_set_wait_limit(uint32_t polls) {
+  polfed::g_wait_limit.store(polls);
+  return POLFED_OK;
+}
 
 extern "C" int polfed_cheb_filter_static(const polfed_model* model, const uint32_t* d_states, int64_t dim,
                                          double e_lo, double e_hi, double sigma, int32_t K, const double* coeffs,

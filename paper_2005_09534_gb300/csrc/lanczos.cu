@@ -90,6 +90,8 @@ struct polfed_ctx {
   polfed_progress_fn progress = nullptr;
   void* progress_user = nullptr;
   int block_steps = 0;  // block-Lanczos steps of the current run (over restarts), for the hook's index
+  std::vector<polfed_conv_point> hist;  // convergence checks of the last call
+  int attempt = 0;                      // attempt index recorded in hist
 };
 
 namespace {
@@ -405,6 +407,18 @@ int run_lanczos(polfed_ctx* c, HamPlan& plan, const LanczosParams& P, double* d_
     out.n_conv = nconv_p;
     out.n_acc = 0;
     for (int i = 0; i < n; i++) out.n_acc += theta[i] >= p;
+    {
+      polfed_conv_point cp;
+      memset(&cp, 0, sizeof(cp));
+      cp.step = j + 1;
+      cp.cols = n;
+      cp.n_conv = nconv_p;
+      cp.n_acc = out.n_acc;
+      cp.attempt = c->attempt;
+      cp.theta_nev = n >= P.N_ev ? theta[ord[P.N_ev - 1]] : -1.0;
+      cp.max_res_top = maxres_top;
+      c->hist.push_back(cp);
+    }
     if (debug_on()) {
       fprintf(stderr, "[polfed dbg] check n=%d: top theta/res:", n);
       for (int k = 0; k < std::min(n, 12); k++) fprintf(stderr, " %.4f/%.1e", theta[ord[k]], tres[ord[k]]);
@@ -866,6 +880,8 @@ int polfed_block_lanczos(polfed_ctx* c, const polfed_model* model, double e_lo, 
   LanczosOut o;
   const double t0 = now_s();
   c->block_steps = 0;
+  c->hist.clear();
+  c->attempt = 0;
   int rc = run_lanczos(c, plan, P, d_evecs, o);
   if (rc != POLFED_OK && rc != POLFED_ENOCONV) return rc;
   const double half = 0.5 * (e_hi - e_lo), mid = 0.5 * (e_hi + e_lo);
@@ -898,6 +914,14 @@ int polfed_block_lanczos(polfed_ctx* c, const polfed_model* model, double e_lo, 
   return rc;
 }
 
+int polfed_ctx_history(polfed_ctx* c, polfed_conv_point* out, int32_t max, int32_t* n) {
+  if (!c || !n) return fail(POLFED_EINVAL, "ctx or n is NULL");
+  *n = (int32_t)c->hist.size();
+  if (out)
+    for (int32_t i = 0; i < std::min<int32_t>(max, *n); i++) out[i] = c->hist[i];
+  return POLFED_OK;
+}
+
 int polfed_ctx_set_progress(polfed_ctx* c, polfed_progress_fn fn, void* user) {
   if (!c) return fail(POLFED_EINVAL, "ctx is NULL");
   c->progress = fn;
@@ -913,6 +937,10 @@ int polfed_eigs(polfed_ctx* c, const polfed_model* model, double eps_target, int
 }  // extern "C"
 
 namespace polfed {
+
+cudaStream_t ctx_stream(polfed_ctx* c) { return c->stream; }
+void* ctx_solver(polfed_ctx* c) { return c->solver; }
+int ctx_device(polfed_ctx* c) { return c->device; }
 
 int eigs_impl(polfed_ctx* c, const polfed_model* model, double eps_target, int32_t N_ev, int32_t K, int32_t n_b,
               const polfed_opts* opts, double* evals, double* d_evecs, double* resid, polfed_stats* stats,
@@ -1024,6 +1052,8 @@ int eigs_impl(polfed_ctx* c, const polfed_model* model, double eps_target, int32
             (long long)dim, Emin, Emax, berr, sigma, mean, gam, rho_t, K);
   // 3. block Lanczos
   c->block_steps = 0;
+  c->hist.clear();
+  c->attempt = 0;
   notify(c, POLFED_PHASE_START, K);
   const int S = round_block(n_b);
   const double hnorm0 = std::max(std::fabs(Emin), std::fabs(Emax));
@@ -1060,6 +1090,7 @@ int eigs_impl(polfed_ctx* c, const polfed_model* model, double eps_target, int32
     K = Kn;
     P.K = K;
     restarts++;
+    c->attempt++;
   }
   if (rc != POLFED_OK && rc != POLFED_ENOCONV) return rc;
   if (mixed && lo.n_out > 0) {
@@ -1067,10 +1098,13 @@ int eigs_impl(polfed_ctx* c, const polfed_model* model, double eps_target, int32
     int Kr = std::max(16, K / 2);
     if (sigma == 0.0) Kr &= ~1;
     double mr_prev = 1e300;
-    for (int sweep = 0; sweep < 4; sweep++) {
+    // sweeps continue to the refinement target (tol_refine, default tol_resid)
+    const double tol_ref_t =
+        (o.tol_refine > 0.0 ? std::min(o.tol_refine, o.tol_resid) : o.tol_resid) * hnorm0 / (0.5 * (e_hi - e_lo));
+    for (int sweep = 0; sweep < 6; sweep++) {
       double mr = 0.0;
       for (double r : lo.resid_t) mr = std::max(mr, r);
-      if (lo.n_out >= N_ev && mr <= P.tol_resid_t && sweep > 0) break;
+      if (lo.n_out >= N_ev && mr <= tol_ref_t && sweep > 0) break;
       if (sweep >= 3 && mr > 0.5 * mr_prev) break;  // stagnating: more sweeps will not help
       mr_prev = mr;
       if (o.verbose || debug_on())
@@ -1099,6 +1133,7 @@ int eigs_impl(polfed_ctx* c, const polfed_model* model, double eps_target, int32
       P2.o.precision = POLFED_DF64;
       P2.o.tol_conv = o.tol_conv;
       P2.accept_any = false;
+      c->attempt++;
       LanczosOut l2;
       rc = run_lanczos(c, plan, P2, d_evecs, l2);
       if (rc != POLFED_OK && rc != POLFED_ENOCONV) return rc;

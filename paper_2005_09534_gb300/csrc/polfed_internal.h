@@ -209,6 +209,11 @@ struct FilterHook {
   virtual int plan_b(int L) { return -1; }  // low/high split for the plans (-1 = default)
   virtual ~FilterHook() {}
 };
+// Context internals for the other translation units.
+cudaStream_t ctx_stream(polfed_ctx* c);
+void* ctx_solver(polfed_ctx* c);  // cusolverDnHandle_t
+int ctx_device(polfed_ctx* c);
+
 // polfed_eigs with an optional hook (nullptr = direct filter launches).
 int eigs_impl(polfed_ctx* c, const polfed_model* model, double eps_target, int32_t N_ev, int32_t K, int32_t n_b,
               const polfed_opts* opts, double* evals, double* d_evecs, double* resid, polfed_stats* stats,

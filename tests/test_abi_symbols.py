@@ -59,7 +59,8 @@ def test_struct_layouts_match_header(tmp_path):
     if shutil.which("gcc") is None:
         pytest.skip("gcc not available")
     structs = [("polfed_model", pf.CModel), ("polfed_opts", pf.COpts), ("polfed_stats", pf.CStats),
-               ("polfed_batch_info", pf.CBatchInfo), ("polfed_counters", pf.CCounters)]
+               ("polfed_batch_info", pf.CBatchInfo), ("polfed_counters", pf.CCounters),
+               ("polfed_conv_point", pf.CConvPoint)]
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "polfed.h"', "int main(void) {"]
     for cname, cls in structs:
         lines.append(f'  printf("{cname} %zu\\n", sizeof({cname}));')

@@ -11,12 +11,12 @@ from gpu_common import lib, torch_dev
 pytestmark = pytest.mark.gpu
 
 
-def _run(pf, torch, dev, m, eps, n_ev, n_b, precision, K=0):
-    import paper_2005_09534_gb300 as pfm
+def _run(pf, torch, dev, m, eps, n_ev, n_b, precision, K=0, tol_refine=0.0):
     dim = pf.basis_build(m.L, m.L // 2)
     vecs = torch.empty((n_ev, dim), dtype=torch.float64, device=dev)  # column-major dim x n_ev
     o = pf.opts_default()
     o.precision = precision
+    o.tol_refine = tol_refine
     with pf.Ctx(0) as ctx:
         ev, res, st, rc = pf.eigs(ctx, m, eps, n_ev, K, n_b, o, d_evecs=vecs)
     return ev, res, st, vecs.cpu().numpy().T
@@ -106,6 +106,44 @@ def test_mixed_precision_f32_stage_with_refinement():
     # entropy follows the eigenvector error (~ residual / level spacing) at
     # first order, which the residual target of 1e-8 ||H|| leaves near 1e-7
     _check(r, ev, res, V, 50, m, se_tol=1e-6)
+
+
+def test_mixed_precision_refined_to_entropy_bar():
+    """The same FP32-stage run with the refinement target at 1e-12 ||H||: the
+    eigenvector error (~ residual / level spacing) then keeps the entanglement
+    entropy within 1e-8 of dense ED, with every other quantity at its bar."""
+    torch, dev = torch_dev()
+    pf = lib()
+    m = I.xxz(14, 3.0, 1, 0)
+    r = O.eigs_nearest(m.L, m.J1, m.J2, m.Delta, m.h, True, 0.5, 50)
+    ev, res, st, V = _run(pf, torch, dev, m, 0.5, 50, 16, pf.F32, tol_refine=1e-12)
+    assert st["n_refine"] >= 1 and st["fallback_df64"] == 0
+    assert np.max(res) <= 1e-11 * r["norm"], np.max(res) / r["norm"]
+    _check(r, ev, res, V, 50, m, se_tol=1e-8)
+    sel = [O.entanglement_entropy(V[:, i], r["states"], m.L) - O.entanglement_entropy(r["evecs"][:, i], r["states"], m.L)
+           for i in range(0, 50, 7)]
+    assert np.max(np.abs(sel)) <= 1e-8
+
+
+def test_free_fermions_open_chain_L22_mixed_precision():
+    """Headline size and path: L = 22 (dim 705432), N_ev = 500, n_b = 64, FP32
+    stage + float-float refinement, at the free-fermion point (Delta = 0,
+    J2 = 0, open chain, W = 3) whose sector spectrum is exact at any L
+    (single-particle subset sums): eigenvalues within 1e-10 ||H||, residuals
+    <= 1e-8 ||H||."""
+    torch, dev = torch_dev()
+    pf = lib()
+    m = I.free_fermion(22, 3.0, 6, 0, periodic=False)
+    E = O.free_fermion_energies(m.L, m.J1, m.h, False)
+    want, _ = O.select_nearest(E, None, O.target_energy(E, 0.5), 500)
+    nrm = max(abs(E[0]), abs(E[-1]))
+    o = pf.opts_default()
+    o.precision = pf.F32
+    with pf.Ctx(0) as ctx:
+        ev, res, st, rc = pf.eigs(ctx, m, 0.5, 500, 0, 64, o)
+    assert abs(st["E_min"] - E[0]) <= 1e-10 * nrm and abs(st["E_max"] - E[-1]) <= 1e-10 * nrm
+    assert np.max(np.abs(ev - want)) <= 1e-10 * nrm, np.max(np.abs(ev - want)) / nrm
+    assert np.max(res) <= 1e-8 * nrm, np.max(res) / nrm
 
 
 def test_config_L20_j1j2_fp32_refined_agrees_with_df64():
