@@ -177,6 +177,21 @@ int polfed_cheb_filter(const polfed_model* model, const uint32_t* d_states, int6
                        double sigma, int32_t K, const double* coeffs, const void* d_X, void* d_Y, int32_t n_b,
                        int32_t dtype, polfed_stream_t stream);
 
+/* Y[:, j] = sum_n coeffs[j (K + 1) + n] T_n(H~) X[:, j]: every column through
+ * its own order-K Chebyshev series (the Clenshaw recurrence of the text after
+ * Eq. (4) with per-column coefficients).  POLFED's mixed-precision refinement
+ * uses it for the divided differences g_j(x) = (P(x) - P(lam_j)) / (x - lam_j)
+ * of Eq. (2)'s transform at each Ritz value lam_j, applied to the residuals.
+ *   K      : 1 <= K <= 10^7.
+ *   coeffs : HOST array of n_b (K + 1) doubles, column j's series at coeffs + j (K + 1).
+ *   d_X, d_Y : device, row-major dim x n_b FP32 (dtype is FP32 only).
+ *   other arguments as in polfed_h_apply.
+ * Synchronizes the stream before returning.  POLFED_EBOUNDS if the output is
+ * not finite. */
+int polfed_cheb_filter_cols(const polfed_model* model, const uint32_t* d_states, int64_t dim, double e_lo,
+                            double e_hi, int32_t K, const double* coeffs, const void* d_X, void* d_Y, int32_t n_b,
+                            polfed_stream_t stream);
+
 /* Allocation-free variant of polfed_cheb_filter (the paper has no
  * counterpart; this is a service for callers).  Some callers cannot allocate
  * device memory while they run: code executing inside an allocator or memory

@@ -35,7 +35,7 @@ PHASE_START, PHASE_BLOCK, PHASE_REFINE, PHASE_END = 0, 1, 2, 3
 PROGRESS_FN = ctypes.CFUNCTYPE(None, c_void_p, c_int32, c_int32)
 
 EXPORTED = ["polfed_opts_default", "polfed_basis_build", "polfed_h_apply", "polfed_cheb_filter",
-            "polfed_cheb_filter_static",
+            "polfed_cheb_filter_cols", "polfed_cheb_filter_static",
             "polfed_ctx_create", "polfed_ctx_destroy", "polfed_ctx_set_stream", "polfed_ctx_set_progress",
             "polfed_get_counters", "polfed_ctx_history", "polfed_block_lanczos",
             "polfed_eigs", "polfed_spectral_bounds", "polfed_kpm_moments", "polfed_kpm_count",
@@ -132,6 +132,8 @@ def load(path: str = LIB_PATH):
     lib.polfed_cheb_filter.argtypes = [POINTER(CModel), c_void_p, c_int64, c_double, c_double, c_double, c_int32,
                                        POINTER(c_double), c_void_p, c_void_p, c_int32, c_int32, c_void_p]
     lib.polfed_cheb_filter_static.argtypes = lib.polfed_cheb_filter.argtypes
+    lib.polfed_cheb_filter_cols.argtypes = [POINTER(CModel), c_void_p, c_int64, c_double, c_double, c_int32,
+                                            POINTER(c_double), c_void_p, c_void_p, c_int32, c_void_p]
     lib.polfed_ctx_create.argtypes = [c_int32, c_size_t, POINTER(c_void_p)]
     lib.polfed_ctx_destroy.argtypes = [c_void_p]
     lib.polfed_ctx_destroy.restype = None
@@ -249,6 +251,17 @@ def cheb_filter(model, d_states, dim, e_lo, e_hi, sigma, K, X, Y, n_b, dtype, co
     rc = load().polfed_cheb_filter(byref(m.c), _ptr(d_states), int(dim), float(e_lo), float(e_hi), float(sigma),
                                    int(K), cptr, _ptr(X), _ptr(Y), int(n_b), int(dtype), _stream(stream))
     return _check(rc, allow=(POLFED_EBOUNDS,) if allow_bounds_error else ())
+
+
+def cheb_filter_cols(model, d_states, dim, e_lo, e_hi, coeffs, X, Y, n_b, stream=None):
+    """polfed_cheb_filter_cols: FP32 filter, column j through its own series coeffs[j] (n_b x (K + 1))."""
+    m = Model.of(model)
+    coeffs = np.ascontiguousarray(np.asarray(coeffs, dtype=np.float64))
+    assert coeffs.ndim == 2 and coeffs.shape[0] == int(n_b)
+    K = coeffs.shape[1] - 1
+    return _check(load().polfed_cheb_filter_cols(byref(m.c), _ptr(d_states), int(dim), float(e_lo), float(e_hi),
+                                                 int(K), coeffs.ctypes.data_as(POINTER(c_double)), _ptr(X), _ptr(Y),
+                                                 int(n_b), _stream(stream)))
 
 
 def cheb_filter_static(model, d_states, dim, e_lo, e_hi, sigma, K, X, Y, n_b, dtype, coeffs=None, stream=None):

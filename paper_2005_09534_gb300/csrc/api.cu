@@ -174,4 +174,45 @@ int polfed_cheb_filter(const polfed_model* model, const uint32_t* d_states, int6
   return POLFED_OK;
 }
 
+int polfed_cheb_filter_cols(const polfed_model* model, const uint32_t* d_states, int64_t dim, double e_lo,
+                            double e_hi, int32_t K, const double* coeffs, const void* d_X, void* d_Y, int32_t n_b,
+                            polfed_stream_t stream) {
+  clear_error();
+  PF_CHECK(check_block_args(model, d_states, dim, d_X, d_Y, n_b, POLFED_F32));
+  PF_CHECK(check_bounds(e_lo, e_hi));
+  if (K < 1 || K > 10000000) return fail(POLFED_EINVAL, "K must be in 1..1e7");
+  if (!coeffs) return fail(POLFED_EINVAL, "coeffs is NULL");
+  const int W = slice_width(POLFED_F32, choose_lpr(POLFED_F32, n_b));
+  const int nsl = (n_b + W - 1) / W;
+  std::vector<float> cf((size_t)nsl * (K + 1) * W, 0.f);
+  for (int j = 0; j < n_b; j++)
+    for (int n = 0; n <= K; n++) {
+      const double v = coeffs[(size_t)j * (K + 1) + n];
+      if (!std::isfinite(v)) return fail(POLFED_EINVAL, "non-finite coefficient");
+      cf[((size_t)(j / W) * (K + 1) + n) * W + (j % W)] = (float)v;
+    }
+  cudaStream_t s = (cudaStream_t)stream;
+  HamPlan plan;
+  PF_CHECK(plan.init(model, s, true));
+  PF_CHECK(plan.prepare_typed(POLFED_F32, e_lo, e_hi));
+  const int lpr = choose_lpr(POLFED_F32, n_b);
+  StreamScratch mem, cmem;
+  mem.s = s;
+  cmem.s = s;
+  FilterScratch scr;
+  scr.bytes = filter_scratch_bytes(plan, POLFED_F32, lpr);
+  PF_CUDA(cudaMallocAsync(&mem.p, scr.bytes, s));
+  scr.xs = mem.p;
+  PF_CUDA(cudaMallocAsync(&cmem.p, cf.size() * sizeof(float), s));
+  PF_CUDA(cudaMemcpyAsync(cmem.p, cf.data(), cf.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+  PF_CHECK(filter_block_cols(plan, (const float*)cmem.p, K, d_X, d_Y, n_b, POLFED_F32, scr, s));
+  float flag[3] = {0, 0, 0};
+  PF_CUDA(cudaMemcpyAsync(flag, scr.flag, sizeof(flag), cudaMemcpyDeviceToHost, s));
+  PF_CUDA(cudaStreamSynchronize(s));
+  int bad = 0;
+  memcpy(&bad, &flag[2], 4);
+  if (bad) return fail(POLFED_EBOUNDS, "filter output is not finite: spectrum outside [e_lo, e_hi]");
+  return POLFED_OK;
+}
+
 }  // extern "C"

@@ -205,6 +205,23 @@ __global__ void k_tables_rec(const HamGeometry g, const uint16_t* T_lo, uint16_t
   for (int k = 0; k < g.n_cross; k++) r[RS - 1 - k] = T_lo[a ^ (1 << g.cross_lo[k])];
 }
 
+// One-byte copy of the neighbour records (layout in HamTables::rec8).
+__global__ void k_tables_rec8(const HamGeometry g, const uint16_t* rec, uint8_t* rec8) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= (1 << g.b)) return;
+  const int RS = g.rec_stride;
+  const uint16_t* r = rec + (size_t)a * RS;
+  uint8_t* o = rec8 + (size_t)a * RS;
+  for (int e = 0; e < RS; e++) o[e] = 0;
+  const int n1 = r[1] & 0xFF, n2 = r[1] >> 8;
+  o[0] = (uint8_t)(r[0] & 0xFF);
+  o[1] = (uint8_t)(r[0] >> 8);
+  o[2] = (uint8_t)n1;
+  o[3] = (uint8_t)n2;
+  for (int k = 0; k < n1 + n2; k++) o[4 + k] = (uint8_t)r[2 + k];
+  for (int k = 0; k < g.n_cross; k++) o[RS - 1 - k] = (uint8_t)r[RS - 1 - k];
+}
+
 // Per-group constants in schedule order.
 __global__ void k_tables_groups(const HamGeometry g, const int32_t* T_hi, const int32_t* order, GroupRec* gr) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -330,11 +347,11 @@ struct NF32 {
   static __device__ __forceinline__ void acc(A& a, S v) { a += v; }
   static __device__ __forceinline__ C add3(C a, C b, C c) { return a + b + c; }
   static __device__ __forceinline__ S combine(S xv, S x1, S b2v, A a1, A a2, C ad, const KC& k, bool hx, bool hb,
-                                              bool j2) {
+                                              bool j2, C cx) {
     float y = ad * x1 + k.o1 * a1;
     if (j2) y = fmaf(k.o2, a2, y);
     float r = k.cH * y;
-    if (hx) r = fmaf(k.cX, xv, r);
+    if (hx) r = fmaf(cx, xv, r);
     if (hb) r = fmaf(k.cB, b2v, r);
     return r;
   }
@@ -350,11 +367,11 @@ struct NF64 {
   static __device__ __forceinline__ void acc(A& a, S v) { a += v; }
   static __device__ __forceinline__ C add3(C a, C b, C c) { return a + b + c; }
   static __device__ __forceinline__ S combine(S xv, S x1, S b2v, A a1, A a2, C ad, const KC& k, bool hx, bool hb,
-                                              bool j2) {
+                                              bool j2, C cx) {
     double y = ad * x1 + k.o1 * a1;
     if (j2) y = fma(k.o2, a2, y);
     double r = k.cH * y;
-    if (hx) r = fma(k.cX, xv, r);
+    if (hx) r = fma(cx, xv, r);
     if (hb) r = fma(k.cB, b2v, r);
     return r;
   }
@@ -374,22 +391,31 @@ struct NDF {
   }
   static __device__ __forceinline__ C add3(C a, C b, C c) { return df_add(df_add(a, b), c); }
   static __device__ __forceinline__ S combine(S xv, S x1, S b2v, A a1, A a2, C ad, const KC& k, bool hx, bool hb,
-                                              bool j2) {
+                                              bool j2, C cx) {
     float2 y = df_add(df_mul(ad, x1), df_mul(k.o1, fast_two_sum(a1.x, a1.y)));
     if (j2) y = df_add(y, df_mul(k.o2, fast_two_sum(a2.x, a2.y)));
     if (k.exact) {
       float2 r = make_float2(k.cH.x * y.x, k.cH.x * y.y);
-      if (hx) r = df_add(r, make_float2(k.cX.x * xv.x, k.cX.x * xv.y));
+      if (hx) r = df_add(r, make_float2(cx.x * xv.x, cx.x * xv.y));
       if (hb) r = df_add(r, make_float2(k.cB.x * b2v.x, k.cB.x * b2v.y));
       return r;
     }
     float2 r = df_mul(k.cH, y);
-    if (hx) r = df_add(r, df_mul(k.cX, xv));
+    if (hx) r = df_add(r, df_mul(cx, xv));
     if (hb) r = df_add(r, df_mul(k.cB, b2v));
     return r;
   }
   static __device__ __forceinline__ float mag(S v) { return fabsf(v.x); }
 };
+
+// cX of the lane's element e: the per-column array (FP32 storage only) or the step's scalar
+template <class NT>
+__device__ __forceinline__ typename NT::C col_cx(const float* cxcol, int col, const typename NT::KC& kc) {
+  if constexpr (std::is_same<NT, NF32>::value) {
+    if (cxcol) return __ldg(cxcol + col);
+  }
+  return kc.cX;
+}
 
 template <class S>
 union V16 {
@@ -397,9 +423,27 @@ union V16 {
   S s[16 / sizeof(S)];
 };
 
+// acc[0..VEC) += the elements of one 16-byte chunk; FP32 uses the packed
+// two-wide add of sm_100+ (two additions per instruction, same rounding)
+template <class NT>
+__device__ __forceinline__ void acc_chunk(typename NT::A* acc, const V16<typename NT::S>& u) {
+  if constexpr (std::is_same<NT, NF32>::value) {
+    float2 p0 = __fadd2_rn(make_float2(acc[0], acc[1]), make_float2(u.s[0], u.s[1]));
+    float2 p1 = __fadd2_rn(make_float2(acc[2], acc[3]), make_float2(u.s[2], u.s[3]));
+    acc[0] = p0.x;
+    acc[1] = p0.y;
+    acc[2] = p1.x;
+    acc[3] = p1.y;
+  } else {
+#pragma unroll
+    for (int v = 0; v < (int)(16 / sizeof(typename NT::S)); v++) NT::acc(acc[v], u.s[v]);
+  }
+}
+
 // ---------------------------------------------------------- the step kernel
 struct StepTables {
   const uint16_t* rec;
+  const uint8_t* rec8;
   const GroupRec* grec;
   const void* F_lo;  // typed, alpha-scaled
   const void* F_hi;  // typed, alpha-scaled, includes -alpha*beta (indexed by s_hi)
@@ -431,7 +475,7 @@ __device__ __forceinline__ void step_group(const int gidx, const int n_cross, co
                                            const typename NT::S* b2, const typename NT::S* __restrict__ x,
                                            typename NT::S* out, const typename NT::KC& kc, const int has_x,
                                            const int has_b2, typename NT::S* tile, const typename NT::C* sFlo,
-                                           const typename NT::C* sCx) {
+                                           const typename NT::C* sCx, const float* cxcol) {
   using S = typename NT::S;
   using C = typename NT::C;
   using A = typename NT::A;
@@ -618,7 +662,7 @@ __device__ __forceinline__ void step_group(const int gidx, const int n_cross, co
 #pragma unroll
           for (int v = 0; v < VEC; v++)
             res.s[v] = NT::combine(has_x ? xv[j].s[v] : S(), xo.s[v], has_b2 ? bv[j].s[v] : S(), a1[i][v],
-                                   a2[i][v], ad, kc, has_x, has_b2, J2);
+                                   a2[i][v], ad, kc, has_x, has_b2, J2, col_cx<NT>(cxcol, lane * VEC + v, kc));
           __stcg(reinterpret_cast<int4*>(out + off), res.i);
         }
       }
@@ -639,7 +683,7 @@ __global__ void __launch_bounds__(256, 2) k_ham_step(const HamGeometry g, const 
                                                       const typename NT::S* __restrict__ b1,
                                                       const typename NT::S* b2, const typename NT::S* __restrict__ x,
                                                       typename NT::S* out, const typename NT::KC kc, int has_x,
-                                                      int has_b2) {
+                                                      int has_b2, const float* cxcol) {
   using S = typename NT::S;
   using C = typename NT::C;
   using A = typename NT::A;
@@ -672,7 +716,7 @@ __global__ void __launch_bounds__(256, 2) k_ham_step(const HamGeometry g, const 
 
   for (int gidx = blockIdx.x; gidx < g.n_groups; gidx += gridDim.x)
     step_group<NT, LPR, J2, false>(gidx, g.n_cross, cr_lb, cr_c2, t, b1, b2, x, out, kc, has_x, has_b2, tile, sFlo,
-                                   sCx);
+                                   sCx, cxcol);
 }
 
 // -------------------------------------------------------- bounded waits
@@ -821,7 +865,7 @@ __global__ void __launch_bounds__(256, 2)
         make_kc<NT>(cX, cH, cB, J.o1, J.o2, kc);
         step_group<NT, LPR, J2, true>(w - base, n_cross, cr_lb, cr_c2, J.t, cur, oth,
                                       reinterpret_cast<const S*>(J.xs), oth, kc, cX != 0.0, cB != 0.0, tile, sFlo,
-                                      sCx);
+                                      sCx, nullptr);
       }
       base += ng;
     }
@@ -869,35 +913,49 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile
   return false;
 }
 
-constexpr int kTmaConsumerWarps = 16;
-constexpr int kTmaThreads = 32 * (kTmaConsumerWarps + 1);  // warp 0 issues the copies
-constexpr int kTmaRowsPerThread = 2;  // 128 row units x 2 = 256 rows >= C(10,5) = 252
-__host__ __device__ constexpr int tma_stages(bool j2) { return j2 ? 2 : 3; }
+// Shapes of the kernel: CW consumer warps (plus the producer warp), LPR lanes
+// per 128-byte row (4: two 16-byte chunks per lane; 8: one chunk per lane),
+// RPT rows per lane, RPT * 32 CW / LPR >= C(10, 5) = 252 rows (the largest group).
+template <int CW_, int LPR_>
+struct TmaShape {
+  static constexpr int CW = CW_;
+  static constexpr int LPR = LPR_;
+  static constexpr int THREADS = 32 * (CW + 1);  // warp 0 issues the copies
+  static constexpr int UNITS = 32 * CW / LPR;
+  static constexpr int RPT = (252 + UNITS - 1) / UNITS;
+};
+using TmaShapeA = TmaShape<16, 4>;  // 544 threads, 2 rows of 2 chunks per lane
+using TmaShapeB = TmaShape<24, 8>;  // 800 threads, 3 rows of 1 chunk per lane
+__host__ __device__ constexpr int tma_stages(bool j2) { return j2 ? 3 : 4; }
 
-template <class NT, bool J2>
-__global__ void __launch_bounds__(kTmaThreads, 1)
+template <class NT, bool J2, class SH>
+__global__ void __launch_bounds__(SH::THREADS, 1)
     k_ham_step_tma(const HamGeometry g, const StepTables t, const typename NT::S* __restrict__ b1,
                    const typename NT::S* b2, const typename NT::S* __restrict__ x, typename NT::S* out,
-                   const typename NT::KC kc, int has_x, int has_b2, int* err, uint32_t wait_cap) {
+                   const typename NT::KC kc, int has_x, int has_b2, int* err, uint32_t wait_cap,
+                   const float* cxcol) {
   using S = typename NT::S;
   using C = typename NT::C;
   using A = typename NT::A;
-  constexpr int LPR = 4;             // lanes per 128-byte row
-  constexpr int VEC = 16 / sizeof(S);  // elements per 16-byte chunk
-  constexpr int W = 2 * VEC * LPR;     // elements per row (two chunks per lane)
-  constexpr int VL = 2 * VEC;          // elements per lane
+  constexpr int LPR = SH::LPR;          // lanes per 128-byte row
+  constexpr int VEC = 16 / sizeof(S);   // elements per 16-byte chunk
+  constexpr int NCH = 8 / LPR;          // 16-byte chunks per lane
+  constexpr int W = 8 * VEC;            // elements per 128-byte row
+  constexpr int VL = NCH * VEC;         // elements per lane
   constexpr int MAXCR = J2 ? 6 : 2;
-  constexpr int RS = J2 ? 32 : 16;
-  constexpr int LOWMAX = RS - 2 - MAXCR;
+  constexpr int RS = J2 ? 32 : 16;  // bytes per record
+  constexpr int LOWMAX = RS - 4 - MAXCR;
   constexpr int NS = tma_stages(J2);
-  constexpr int RPT = kTmaRowsPerThread;
-  constexpr int UNITS = 32 * kTmaConsumerWarps / LPR;
+  constexpr int RPT = SH::RPT;
+  constexpr int UNITS = SH::UNITS;
+  constexpr int kThreads = SH::THREADS;
+  constexpr int kConsumerWarps = SH::CW;
 
   extern __shared__ __align__(128) unsigned char smem[];
   const size_t stg = (size_t)g.max_group * W;  // elements per stage
   S* own = reinterpret_cast<S*>(smem);         // [2][stg]
   S* ring = own + 2 * stg;                     // [NS][stg]
-  uint16_t* sRec = reinterpret_cast<uint16_t*>(ring + NS * stg);  // [2^b][RS] neighbour records
+  uint8_t* sRec = reinterpret_cast<uint8_t*>(ring + NS * stg);  // [2^b][RS] one-byte neighbour records
   C* sFlo = reinterpret_cast<C*>(sRec + ((size_t)RS << g.b));
   C* sCx = sFlo + (1 << g.b);
   __shared__ __align__(8) uint64_t own_full[2], own_empty[2], full[NS], empty[NS];
@@ -908,24 +966,24 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
   if (tid == 0) {
     for (int i = 0; i < 2; i++) {
       mbar_init(&own_full[i], 1);
-      mbar_init(&own_empty[i], kTmaConsumerWarps);
+      mbar_init(&own_empty[i], kConsumerWarps);
     }
     for (int i = 0; i < NS; i++) {
       mbar_init(&full[i], 1);
-      mbar_init(&empty[i], kTmaConsumerWarps);
+      mbar_init(&empty[i], kConsumerWarps);
     }
     s_abort = 0;
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   {
-    const uint4* src = reinterpret_cast<const uint4*>(t.rec);
+    const uint4* src = reinterpret_cast<const uint4*>(t.rec8);
     uint4* dst = reinterpret_cast<uint4*>(sRec);
-    const int n16 = (RS * 2 << g.b) / 16;
-    for (int i = tid; i < n16; i += kTmaThreads) dst[i] = __ldg(src + i);
+    const int n16 = (RS << g.b) / 16;
+    for (int i = tid; i < n16; i += kThreads) dst[i] = __ldg(src + i);
     const C* gFlo = reinterpret_cast<const C*>(t.F_lo);
     const C* gCx = reinterpret_cast<const C*>(t.C_x);
-    for (int i = tid; i < (1 << g.b); i += kTmaThreads) sFlo[i] = gFlo[i];
-    for (int i = tid; i < (1 << g.n_cross); i += kTmaThreads) sCx[i] = gCx[i];
+    for (int i = tid; i < (1 << g.b); i += kThreads) sFlo[i] = gFlo[i];
+    for (int i = tid; i < (1 << g.n_cross); i += kThreads) sCx[i] = gCx[i];
   }
   __syncthreads();
   const int n_my = (g.n_groups - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
@@ -1021,9 +1079,21 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
   // -------------------------------------------------------------- consumers
   const int ctid = tid - 32;
   const int unit = ctid / LPR, lane = ctid % LPR;
-  // the two 16-byte chunks of a lane, ordered so that the two rows read by a
-  // quarter-warp fall on disjoint shared-memory banks
-  const int ch0 = (lane + 4 * (unit & 1)) * VEC, ch1 = (lane + 4 * (1 - (unit & 1))) * VEC;
+  // the 16-byte chunks of a lane (element offsets in the row); with two chunks
+  // they are ordered so that the two rows read by a quarter-warp fall on
+  // disjoint shared-memory banks
+  int chk[NCH];
+  if constexpr (NCH == 2) {
+    chk[0] = (lane + 4 * (unit & 1)) * VEC;
+    chk[1] = (lane + 4 * (1 - (unit & 1))) * VEC;
+  } else {
+    chk[0] = lane * VEC;
+  }
+  C cxl[VL];  // cX of the lane's elements (per column, or the step's scalar)
+#pragma unroll
+  for (int h = 0; h < NCH; h++)
+#pragma unroll
+    for (int v = 0; v < VEC; v++) cxl[h * VEC + v] = col_cx<NT>(cxcol, chk[h] + v, kc);
   const C* gFhi = reinterpret_cast<const C*>(t.F_hi);
   int cr_lb[MAXCR], cr_c2[MAXCR];
 #pragma unroll
@@ -1031,16 +1101,13 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
     cr_lb[k] = k < g.n_cross ? g.cross_lo[k] : 0;
     cr_c2[k] = k < g.n_cross && g.cross_cls[k] == 2;
   }
-  // accumulate the lane's two chunks of row `row` of buffer `p` into acc
+  // accumulate the lane's chunks of row `row` of buffer `p` into acc
   auto acc2 = [&](A* acc, const S* p, size_t row) {
-    V16<S> u0, u1;
-    u0.i = *reinterpret_cast<const int4*>(p + row * W + ch0);
-    u1.i = *reinterpret_cast<const int4*>(p + row * W + ch1);
+    V16<S> u[NCH];
 #pragma unroll
-    for (int v = 0; v < VEC; v++) {
-      NT::acc(acc[v], u0.s[v]);
-      NT::acc(acc[VEC + v], u1.s[v]);
-    }
+    for (int h = 0; h < NCH; h++) u[h].i = *reinterpret_cast<const int4*>(p + row * W + chk[h]);
+#pragma unroll
+    for (int h = 0; h < NCH; h++) acc_chunk<NT>(acc + h * VEC, u[h]);
   };
   int q = 0;  // ring items consumed
   C fhi_next = gFhi[blockIdx.x];  // diagonal constant of the group, schedule order (prefetched)
@@ -1068,21 +1135,20 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
     for (int i = 0; i < RPT; i++) {
       const int row = unit + UNITS * i;
       const bool live = row < n_g;
-      const uint16_t* r = sRec + (size_t)(cls_base + (live ? row : 0)) * RS;
-      uint32_t rw[RS / 2];
+      const uint8_t* r = sRec + (size_t)(cls_base + (live ? row : 0)) * RS;
+      uint32_t rw[RS / 4];
 #pragma unroll
-      for (int qq = 0; qq < RS / 8; qq++) {
+      for (int qq = 0; qq < RS / 16; qq++) {
         const uint4 v = reinterpret_cast<const uint4*>(r)[qq];
         rw[4 * qq] = v.x;
         rw[4 * qq + 1] = v.y;
         rw[4 * qq + 2] = v.z;
         rw[4 * qq + 3] = v.w;
       }
-#define PF_E(e) ((rw[(e) >> 1] >> (((e)&1) * 16)) & 0xFFFFu)
-      const uint32_t s_lo = PF_E(0);
-      const uint32_t cnt = PF_E(1);
-      const int n1 = live ? (int)(cnt & 0xFF) : 0;
-      const int nl = live ? n1 + (J2 ? (int)(cnt >> 8) : 0) : 0;
+#define PF_E(e) ((rw[(e) >> 2] >> (((e)&3) * 8)) & 0xFFu)
+      const uint32_t s_lo = rw[0] & 0xFFFFu;
+      const int n1 = live ? (int)PF_E(2) : 0;
+      const int nl = live ? n1 + (J2 ? (int)PF_E(3) : 0) : 0;
       uint32_t pattern = 0;
 #pragma unroll
       for (int k = 0; k < MAXCR; k++)
@@ -1092,14 +1158,14 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
 #pragma unroll
       for (int k0 = 0; k0 < LOWMAX; k0 += 2) {
         if (k0 >= nmax) break;
-        V16<S> u[2][2];
+        V16<S> u[2][NCH];
 #pragma unroll
         for (int j = 0; j < 2; j++) {
           const int k = k0 + j;
           if (k < LOWMAX && k < nl) {
-            const size_t rr = (size_t)PF_E(2 + k) * W;
-            u[j][0].i = *reinterpret_cast<const int4*>(tile + rr + ch0);
-            u[j][1].i = *reinterpret_cast<const int4*>(tile + rr + ch1);
+            const size_t rr = (size_t)PF_E(4 + k) * W;
+#pragma unroll
+            for (int h = 0; h < NCH; h++) u[j][h].i = *reinterpret_cast<const int4*>(tile + rr + chk[h]);
           }
         }
 #pragma unroll
@@ -1108,10 +1174,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
           if (k < LOWMAX && k < nl) {
             A* acc = (!J2 || k < n1) ? a1[i] : a2[i];
 #pragma unroll
-            for (int v = 0; v < VEC; v++) {
-              NT::acc(acc[v], u[j][0].s[v]);
-              NT::acc(acc[VEC + v], u[j][1].s[v]);
-            }
+            for (int h = 0; h < NCH; h++) acc_chunk<NT>(acc + h * VEC, u[j][h]);
           }
         }
       }
@@ -1130,7 +1193,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
       for (int i = 0; i < RPT; i++) {
         if ((key[i] >> (16 + k)) & 1u) {
           const int row = unit + UNITS * i;
-          const uint16_t* r = sRec + (size_t)(cls_base + row) * RS;
+          const uint8_t* r = sRec + (size_t)(cls_base + row) * RS;
           acc2(c1 ? a1[i] : a2[i], blk, r[RS - 1 - k]);
         }
       }
@@ -1174,8 +1237,8 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
         const uint32_t s_lo = key[i] & 0xFFFFu, pattern = key[i] >> 16;
         const C ad = NT::add3(sFlo[s_lo], fhi, sCx[pattern]);
 #pragma unroll
-        for (int h = 0; h < 2; h++) {
-          const size_t lo = (size_t)row * W + (h ? ch1 : ch0);
+        for (int h = 0; h < NCH; h++) {
+          const size_t lo = (size_t)row * W + chk[h];
           V16<S> xo, xv, bv, res;
           xo.i = *reinterpret_cast<const int4*>(tile + lo);
           if (has_x) xv.i = *reinterpret_cast<const int4*>(ring + (size_t)x_slot * stg + lo);
@@ -1183,8 +1246,8 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
 #pragma unroll
           for (int v = 0; v < VEC; v++)
             res.s[v] = NT::combine(has_x ? xv.s[v] : S(), xo.s[v], has_b2 ? bv.s[v] : S(), a1[i][h * VEC + v],
-                                   a2[i][h * VEC + v], ad, kc, has_x, has_b2, J2);
-          __stcg(reinterpret_cast<int4*>(out + (size_t)(r0 + row) * W + (h ? ch1 : ch0)), res.i);
+                                   a2[i][h * VEC + v], ad, kc, has_x, has_b2, J2, cxl[h * VEC + v]);
+          __stcg(reinterpret_cast<int4*>(out + (size_t)(r0 + row) * W + chk[h]), res.i);
         }
       }
     }
@@ -1232,13 +1295,21 @@ struct Conv<NDF> {
   static __device__ __forceinline__ float2 zero() { return make_float2(0.f, 0.f); }
 };
 
+template <class NT>
+__device__ __forceinline__ typename NT::C col_cx_scale(const float* colscale, int c, typename NT::C cscale) {
+  if constexpr (std::is_same<NT, NF32>::value) {
+    if (colscale) return colscale[c];
+  }
+  return cscale;
+}
+
 // Load columns [col0, col0+ncols) of a row-major ABI block (ld elements per
 // row) into a slice buffer (zero padded to W columns), optionally also write a
 // scaled copy and a zero buffer; records max |x| in flag[0] (as float bits).
 template <class NT, class In>
 __global__ void k_slice_in(const In* __restrict__ in, int64_t dim, int ld, int col0, int ncols, int W,
                            typename NT::S* xs, typename NT::S* a_scaled, typename NT::S* zero_buf,
-                           typename NT::C cscale, float* flag) {
+                           typename NT::C cscale, float* flag, const float* colscale) {
   using S = typename NT::S;
   float mx = 0.f;
   const int64_t n = dim * W;
@@ -1259,7 +1330,7 @@ __global__ void k_slice_in(const In* __restrict__ in, int64_t dim, int ld, int c
       v = Conv<NT>::zero();
     }
     if (xs) xs[e] = v;
-    if (a_scaled) a_scaled[e] = Conv<NT>::mul(cscale, v);
+    if (a_scaled) a_scaled[e] = Conv<NT>::mul(col_cx_scale<NT>(colscale, c, cscale), v);
     if (zero_buf) zero_buf[e] = Conv<NT>::zero();
   }
   for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -1328,7 +1399,7 @@ int HamPlan::init(const polfed_model* m, cudaStream_t s, bool stream_ordered, in
   const size_t oTlo = carve(nlo * 2), oUlo = carve(nlo * 2), oThi = carve(nhi * 4), oOrd = carve(nhi * 4),
                oFlo = carve(nlo * 8), oFhi = carve(nhi * 8), oCx = carve(ncx * 8),
                oRec = carve(nlo * (size_t)geo.rec_stride * 2), oGrp = carve((size_t)geo.n_groups * sizeof(GroupRec)),
-               oErr = carve(64);
+               oErr = carve(64), oRec8 = carve(nlo * (size_t)geo.rec_stride);
   stream_alloc = stream_ordered;
   if (stream_ordered)
     PF_CUDA(cudaMallocAsync(&dev, bytes, s));
@@ -1344,10 +1415,12 @@ int HamPlan::init(const polfed_model* m, cudaStream_t s, bool stream_ordered, in
   tab.C_x = (double*)(d + oCx);
   tab.rec = (uint16_t*)(d + oRec);
   tab.grec = (GroupRec*)(d + oGrp);
+  tab.rec8 = (uint8_t*)(d + oRec8);
   err_flag = (int*)(d + oErr);
   PF_CUDA(cudaMemsetAsync(err_flag, 0, 64, s));
   k_tables_lo<<<(unsigned)((nlo + 255) / 256), 256, 0, s>>>(geo, tab.T_lo, tab.U_lo, tab.F_lo);
   k_tables_rec<<<(unsigned)((nlo + 255) / 256), 256, 0, s>>>(geo, tab.T_lo, tab.rec);
+  k_tables_rec8<<<(unsigned)((nlo + 255) / 256), 256, 0, s>>>(geo, tab.rec, tab.rec8);
   k_tables_hi<<<(unsigned)((nhi + 255) / 256), 256, 0, s>>>(geo, tab.T_hi, tab.F_hi);
   k_tables_cx<<<(unsigned)((ncx + 255) / 256), 256, 0, s>>>(geo, tab.C_x);
   PF_CUDA(cudaGetLastError());
@@ -1435,6 +1508,9 @@ int HamPlan::prepare_typed(int kind, double e_lo, double e_hi) {
 }
 
 void HamPlan::release() {
+  for (StepGraph& gr : graphs)
+    if (gr.exec) cudaGraphExecDestroy(gr.exec);
+  graphs.clear();
   if (dev) {
     if (stream_alloc)
       cudaFreeAsync(dev, stream);
@@ -1524,7 +1600,7 @@ static int launch_step_t(const HamPlan& p, const StepArgs& a, cudaStream_t s) {
   }
   if (occ < 1) return fail(POLFED_EINVAL, "step kernel cannot be resident (shared memory)");
   int grid = std::min(g.n_groups, nsm * occ);
-  StepTables t{p.tab.rec, p.tab.grec, nullptr, nullptr, nullptr, p.tab.order};
+  StepTables t{p.tab.rec, p.tab.rec8, p.tab.grec, nullptr, nullptr, nullptr, p.tab.order};
   if (g.rec_stride != (J2 ? 32 : 16)) return fail(POLFED_EINVAL, "record layout does not match the kernel");
   const size_t es = sizeof(C);
   const char* base = (const char*)p.typed[std::is_same<NT, NF32>::value ? POLFED_F32 : (std::is_same<NT, NF64>::value ? POLFED_F64 : POLFED_DF64)];
@@ -1549,17 +1625,27 @@ static int launch_step_t(const HamPlan& p, const StepArgs& a, cudaStream_t s) {
     kc.o1 = (C)o1;
     kc.o2 = (C)o2;
   }
-  kern<<<grid, threads, smem, s>>>(g, t, (const S*)a.b1, (const S*)a.b2, (const S*)a.x, (S*)a.out, kc,
-                                   a.cX != 0.0 && a.x != nullptr, a.cB != 0.0 && a.b2 != nullptr);
+  const bool hx = a.x != nullptr && (a.cX != 0.0 || a.cxcol != nullptr);
+  kern<<<grid, threads, smem, s>>>(g, t, (const S*)a.b1, (const S*)a.b2, (const S*)a.x, (S*)a.out, kc, hx,
+                                   a.cB != 0.0 && a.b2 != nullptr, a.cxcol);
   PF_CUDA(cudaGetLastError());
-  count_step(kk, (double)g.dim * W * sizeof(S) * (3.0 + (a.cX != 0.0 ? 1.0 : 0.0)));
+  count_step(kk, (double)g.dim * W * sizeof(S) * (3.0 + (hx ? 1.0 : 0.0)));
   return POLFED_OK;
 }
 
 static size_t tma_smem_bytes(const HamGeometry& g, size_t esz_c, bool j2) {
   const size_t stg = (size_t)g.max_group * 128;
-  return (2 + tma_stages(j2)) * stg + ((size_t)g.rec_stride * 2 << g.b) +
+  return (2 + tma_stages(j2)) * stg + ((size_t)g.rec_stride << g.b) +
          (((size_t)1 << g.b) + ((size_t)1 << g.n_cross)) * esz_c;
+}
+
+// Thread shape of the TMA step kernel: 0 = TmaShapeA, 1 = TmaShapeB (POLFED_TMA_SHAPE).
+static int tma_shape() {
+  static const int v = [] {
+    const char* e = getenv("POLFED_TMA_SHAPE");
+    return e ? atoi(e) : 0;
+  }();
+  return v;
 }
 
 static bool tma_disabled() {
@@ -1570,13 +1656,13 @@ static bool tma_disabled() {
   return v;
 }
 
-template <class NT, bool J2>
+template <class NT, bool J2, class SH>
 static int launch_step_tma(const HamPlan& p, const StepArgs& a, cudaStream_t s) {
   using S = typename NT::S;
   using C = typename NT::C;
   const HamGeometry& g = p.geo;
   const size_t smem = tma_smem_bytes(g, sizeof(C), J2);
-  auto kern = k_ham_step_tma<NT, J2>;
+  auto kern = k_ham_step_tma<NT, J2, SH>;
   static LaunchCache cache;  // see launch_step_t
   int dev = 0;
   PF_CUDA(cudaGetDevice(&dev));
@@ -1598,7 +1684,7 @@ static int launch_step_tma(const HamPlan& p, const StepArgs& a, cudaStream_t s) 
   }
   const int grid = std::min(g.n_groups, nsm);
   const int kk = std::is_same<NT, NF32>::value ? POLFED_F32 : (std::is_same<NT, NF64>::value ? POLFED_F64 : POLFED_DF64);
-  StepTables t{p.tab.rec, p.tab.grec, nullptr, nullptr, nullptr, p.tab.order};
+  StepTables t{p.tab.rec, p.tab.rec8, p.tab.grec, nullptr, nullptr, nullptr, p.tab.order};
   const size_t es = sizeof(C);
   const char* base = (const char*)p.typed[kk];
   t.F_lo = base;
@@ -1622,21 +1708,25 @@ static int launch_step_tma(const HamPlan& p, const StepArgs& a, cudaStream_t s) 
     kc.o1 = (C)o1;
     kc.o2 = (C)o2;
   }
-  kern<<<grid, kTmaThreads, smem, s>>>(g, t, (const S*)a.b1, (const S*)a.b2, (const S*)a.x, (S*)a.out, kc,
-                                       a.cX != 0.0 && a.x != nullptr, a.cB != 0.0 && a.b2 != nullptr, p.err_flag,
-                                       wait_cap(kMbarWaitPolls));
+  const bool hx = a.x != nullptr && (a.cX != 0.0 || a.cxcol != nullptr);
+  kern<<<grid, SH::THREADS, smem, s>>>(g, t, (const S*)a.b1, (const S*)a.b2, (const S*)a.x, (S*)a.out, kc, hx,
+                                       a.cB != 0.0 && a.b2 != nullptr, p.err_flag, wait_cap(kMbarWaitPolls), a.cxcol);
   PF_CUDA(cudaGetLastError());
-  count_step(kk, (double)g.dim * 128.0 * (3.0 + (a.cX != 0.0 ? 1.0 : 0.0)));
+  count_step(kk, (double)g.dim * 128.0 * (3.0 + (hx ? 1.0 : 0.0)));
   return POLFED_OK;
 }
 
 template <class NT>
 static int launch_step_n(const HamPlan& p, const StepArgs& a, cudaStream_t s) {
   const bool j2 = p.geo.n_low2 + p.geo.n_high2 > 0 || p.geo.J2 != 0.0;
-  if (a.lpr == 8 && !tma_disabled() && p.geo.max_group <= kTmaRowsPerThread * (32 * kTmaConsumerWarps / 4) &&
+  if (a.lpr == 8 && !tma_disabled() && p.geo.max_group <= 252 &&
+      4 + p.geo.n_low1 + p.geo.n_low2 + (j2 ? 6 : 2) <= p.geo.rec_stride &&
       tma_smem_bytes(p.geo, sizeof(typename NT::C), j2) <= 220 * 1024 && p.geo.max_group >= 32 &&
-      p.geo.rec_stride == (j2 ? 32 : 16))
-    return j2 ? launch_step_tma<NT, true>(p, a, s) : launch_step_tma<NT, false>(p, a, s);
+      p.geo.rec_stride == (j2 ? 32 : 16)) {
+    if (tma_shape() == 1)
+      return j2 ? launch_step_tma<NT, true, TmaShapeB>(p, a, s) : launch_step_tma<NT, false, TmaShapeB>(p, a, s);
+    return j2 ? launch_step_tma<NT, true, TmaShapeA>(p, a, s) : launch_step_tma<NT, false, TmaShapeA>(p, a, s);
+  }
   switch (a.lpr) {
 #define PF_CASE(L_)                                                               \
   case L_:                                                                        \
@@ -1653,6 +1743,7 @@ static int launch_step_n(const HamPlan& p, const StepArgs& a, cudaStream_t s) {
 
 int launch_ham_step(const HamPlan& p, int kind, const StepArgs& a, cudaStream_t s) {
   if (kind < 0 || kind > 2 || !p.typed_ok[kind]) return fail(POLFED_EINVAL, "operator tables not prepared for this precision");
+  if (a.cxcol && kind != POLFED_F32) return fail(POLFED_EINVAL, "per-column coefficients need FP32 storage");
   switch (kind) {
     case POLFED_F32:
       return launch_step_n<NF32>(p, a, s);
@@ -1686,7 +1777,7 @@ static void carve_scratch(FilterScratch& scr, const HamPlan& plan, int kind, int
 
 template <class NT, class In>
 static int slice_in_t(const void* in, int64_t dim, int ld, int col0, int ncols, int W, void* xs, void* as,
-                      void* zb, double scale, float* flag, cudaStream_t s) {
+                      void* zb, double scale, float* flag, cudaStream_t s, const float* colscale) {
   typename NT::C cs;
   if constexpr (std::is_same<NT, NDF>::value)
     split_df(scale, cs);
@@ -1695,25 +1786,26 @@ static int slice_in_t(const void* in, int64_t dim, int ld, int col0, int ncols, 
   const int64_t n = dim * W;
   int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16));
   k_slice_in<NT, In><<<grid, 256, 0, s>>>((const In*)in, dim, ld, col0, ncols, W, (typename NT::S*)xs,
-                                           (typename NT::S*)as, (typename NT::S*)zb, cs, flag);
+                                           (typename NT::S*)as, (typename NT::S*)zb, cs, flag, colscale);
   PF_CUDA(cudaGetLastError());
   count_launch();
   return POLFED_OK;
 }
 
 static int slice_in(int kind, int abi_kind, const void* in, int64_t dim, int ld, int col0, int ncols, int W,
-                    void* xs, void* as, void* zb, double scale, float* flag, cudaStream_t s) {
+                    void* xs, void* as, void* zb, double scale, float* flag, cudaStream_t s,
+                    const float* colscale = nullptr) {
   const bool f32in = abi_kind == POLFED_F32;
   switch (kind) {
     case POLFED_F32:
-      return f32in ? slice_in_t<NF32, float>(in, dim, ld, col0, ncols, W, xs, as, zb, scale, flag, s)
-                   : slice_in_t<NF32, double>(in, dim, ld, col0, ncols, W, xs, as, zb, scale, flag, s);
+      return f32in ? slice_in_t<NF32, float>(in, dim, ld, col0, ncols, W, xs, as, zb, scale, flag, s, colscale)
+                   : slice_in_t<NF32, double>(in, dim, ld, col0, ncols, W, xs, as, zb, scale, flag, s, colscale);
     case POLFED_F64:
-      return f32in ? slice_in_t<NF64, float>(in, dim, ld, col0, ncols, W, xs, as, zb, scale, flag, s)
-                   : slice_in_t<NF64, double>(in, dim, ld, col0, ncols, W, xs, as, zb, scale, flag, s);
+      return f32in ? slice_in_t<NF64, float>(in, dim, ld, col0, ncols, W, xs, as, zb, scale, flag, s, colscale)
+                   : slice_in_t<NF64, double>(in, dim, ld, col0, ncols, W, xs, as, zb, scale, flag, s, colscale);
     default:
-      return f32in ? slice_in_t<NDF, float>(in, dim, ld, col0, ncols, W, xs, as, zb, scale, flag, s)
-                   : slice_in_t<NDF, double>(in, dim, ld, col0, ncols, W, xs, as, zb, scale, flag, s);
+      return f32in ? slice_in_t<NDF, float>(in, dim, ld, col0, ncols, W, xs, as, zb, scale, flag, s, colscale)
+                   : slice_in_t<NDF, double>(in, dim, ld, col0, ncols, W, xs, as, zb, scale, flag, s, colscale);
   }
 }
 
@@ -1792,6 +1884,114 @@ static int check_timeout(HamPlan& plan, cudaStream_t s) {
   return POLFED_OK;
 }
 
+// Launch the Clenshaw steps k = K-1..1 and the final step of Eq. (2) on the
+// scratch slices (b_K in ba, b_{K+1} = 0 in bb, X in xs; result in the buffer
+// the last step writes, returned in *res).
+static int clenshaw_steps(HamPlan& plan, int kind, const double* c, int K, double invD, FilterScratch& scr, int lpr,
+                          cudaStream_t s, void** res) {
+  void* cur = scr.ba;  // b_{k+1}
+  void* oth = scr.bb;  // b_{k+2}, overwritten in place by b_k
+  for (int k = K - 1; k >= 1; k--) {
+    StepArgs a{cur, oth, scr.xs, oth, c[k], 2.0, (k == K - 1) ? 0.0 : -1.0, lpr};
+    PF_CHECK(launch_ham_step(plan, kind, a, s));
+    std::swap(cur, oth);
+  }
+  // Y = (c_0 X + H~ b_1 - b_2) / D
+  StepArgs a{cur, oth, scr.xs, oth, c[0] * invD, invD, (K == 1) ? 0.0 : -invD, lpr};
+  PF_CHECK(launch_ham_step(plan, kind, a, s));
+  *res = oth;
+  return POLFED_OK;
+}
+
+static uint64_t fnv_hash(const double* v, int n) {
+  uint64_t h = 1469598103934665603ull;
+  const unsigned char* b = (const unsigned char*)v;
+  for (size_t i = 0; i < (size_t)n * sizeof(double); i++) h = (h ^ b[i]) * 1099511628211ull;
+  return h;
+}
+
+static bool graphs_disabled() {
+  static const bool v = [] {
+    const char* e = getenv("POLFED_NO_GRAPHS");
+    return e && e[0] == '1';
+  }();
+  return v;
+}
+
+// The recurrence only touches the scratch slices, so one CUDA graph of its K
+// launches serves every slice of every call with the same operator tables,
+// coefficients and scratch: a key seen a second time on a plan is captured
+// once and replayed from then on (kernels of K >= 16 steps).  Counters are
+// credited per replay.
+static int clenshaw_graph(HamPlan& plan, int kind, const double* c, int K, double invD, FilterScratch& scr, int lpr,
+                          cudaStream_t s, void** res) {
+  if (K < 16 || graphs_disabled()) return clenshaw_steps(plan, kind, c, K, invD, scr, lpr, s, res);
+  StepGraph key;
+  key.kind = kind;
+  key.K = K;
+  key.lpr = lpr;
+  key.invD = invD;
+  key.lo = plan.typed_lo[kind];
+  key.hi = plan.typed_hi[kind];
+  key.coef_hash = fnv_hash(c, K + 1);
+  key.wait_cap = wait_cap(kMbarWaitPolls);
+  key.xs = scr.xs;
+  key.ba = scr.ba;
+  key.bb = scr.bb;
+  StepGraph* hit = nullptr;
+  for (StepGraph& gr : plan.graphs)
+    if (gr.kind == key.kind && gr.K == key.K && gr.lpr == key.lpr && gr.invD == key.invD && gr.lo == key.lo &&
+        gr.hi == key.hi && gr.coef_hash == key.coef_hash && gr.wait_cap == key.wait_cap && gr.xs == key.xs &&
+        gr.ba == key.ba && gr.bb == key.bb)
+      hit = &gr;
+  // the result buffer: K - 1 swaps after starting in ba
+  void* out_buf = (K % 2 == 0) ? scr.ba : scr.bb;
+  if (!hit) {  // first sighting: run eagerly, remember the key
+    if (plan.graphs.size() >= 8) {
+      if (plan.graphs.front().exec) cudaGraphExecDestroy(plan.graphs.front().exec);
+      plan.graphs.erase(plan.graphs.begin());
+    }
+    plan.graphs.push_back(key);
+    return clenshaw_steps(plan, kind, c, K, invD, scr, lpr, s, res);
+  }
+  if (!hit->exec) {
+    Counters& cn = counters();
+    const int64_t l0 = cn.launches, n0 = cn.all_launches[kind];
+    const double b0 = cn.all_alg_bytes[kind];
+    cudaGraph_t graph = nullptr;
+    PF_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+    void* r = nullptr;
+    const int rc = clenshaw_steps(plan, kind, c, K, invD, scr, lpr, s, &r);
+    const cudaError_t ec = cudaStreamEndCapture(s, &graph);
+    // the capture executed nothing: take its counts back, credit them per replay
+    hit->launches = cn.all_launches[kind] - n0;
+    hit->alg_bytes = cn.all_alg_bytes[kind] - b0;
+    cn.launches = l0;
+    cn.all_launches[kind] = n0;
+    cn.all_alg_bytes[kind] = b0;
+    if (rc != POLFED_OK || ec != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return rc != POLFED_OK ? rc : fail(POLFED_ECUDA, std::string("stream capture: ") + cudaGetErrorString(ec));
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&hit->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+      hit->exec = nullptr;
+      cudaGetLastError();
+      return fail(POLFED_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ei));
+    }
+  }
+  PF_CUDA(cudaGraphLaunch(hit->exec, s));
+  Counters& cn = counters();
+  cn.launches += hit->launches;
+  cn.all_launches[kind] += hit->launches;
+  cn.all_alg_bytes[kind] += hit->alg_bytes;
+  hit->uses++;
+  *res = out_buf;
+  return POLFED_OK;
+}
+
 int filter_block(HamPlan& plan, int kind, const double* c, int K, double invD, const void* in, void* out, int n_b,
                  int abi_kind, FilterScratch& scr, cudaStream_t s, int lpr_hint) {
   const int lpr = lpr_hint > 0 ? lpr_hint : choose_lpr(kind, n_b);
@@ -1810,16 +2010,42 @@ int filter_block(HamPlan& plan, int kind, const double* c, int K, double invD, c
     }
     // b_K = c_K X (in ba), b_{K+1} = 0 (in bb)
     PF_CHECK(slice_in(kind, abi_kind, in, dim, n_b, col0, ncols, W, scr.xs, scr.ba, scr.bb, c[K], scr.flag, s));
-    void* cur = scr.ba;  // b_{k+1}
-    void* oth = scr.bb;  // b_{k+2}, overwritten in place by b_k
+    void* res = nullptr;
+    StepTimer tm(s, kind);
+    PF_CHECK(clenshaw_graph(plan, kind, c, K, invD, scr, lpr, s, &res));
+    PF_CHECK(tm.stop());
+    PF_CHECK(check_timeout(plan, s));
+    PF_CHECK(slice_out(kind, abi_kind, res, dim, W, ncols, out, n_b, col0, scr.flag, s));
+  }
+  return POLFED_OK;
+}
+
+int filter_block_cols(HamPlan& plan, const float* d_coef, int K, const void* in, void* out, int n_b, int abi_kind,
+                      FilterScratch& scr, cudaStream_t s) {
+  const int kind = POLFED_F32;
+  const int lpr = choose_lpr(kind, n_b);
+  const int W = slice_width(kind, lpr);
+  if (K < 1) return fail(POLFED_EINVAL, "per-column filter needs K >= 1");
+  PF_CHECK(ensure_scratch(scr, filter_scratch_bytes(plan, kind, lpr), plan, kind, lpr));
+  carve_scratch(scr, plan, kind, lpr);
+  const int64_t dim = plan.geo.dim;
+  PF_CUDA(cudaMemsetAsync(scr.flag, 0, 16, s));
+  for (int col0 = 0, q = 0; col0 < n_b; col0 += W, q++) {
+    const int ncols = std::min(W, n_b - col0);
+    const float* cq = d_coef + (size_t)q * (K + 1) * W;  // rows n = 0..K of this slice's W columns
+    // b_K = c_K X (per column), b_{K+1} = 0
+    PF_CHECK(slice_in(kind, abi_kind, in, dim, n_b, col0, ncols, W, scr.xs, scr.ba, scr.bb, 1.0, scr.flag, s,
+                      cq + (size_t)K * W));
+    void* cur = scr.ba;
+    void* oth = scr.bb;
     StepTimer tm(s, kind);
     for (int k = K - 1; k >= 1; k--) {
-      StepArgs a{cur, oth, scr.xs, oth, c[k], 2.0, (k == K - 1) ? 0.0 : -1.0, lpr};
+      StepArgs a{cur, oth, scr.xs, oth, 1.0, 2.0, (k == K - 1) ? 0.0 : -1.0, lpr, cq + (size_t)k * W};
       PF_CHECK(launch_ham_step(plan, kind, a, s));
       std::swap(cur, oth);
     }
-    // Y = (c_0 X + H~ b_1 - b_2) / D
-    StepArgs a{cur, oth, scr.xs, oth, c[0] * invD, invD, (K == 1) ? 0.0 : -invD, lpr};
+    // Y = c_0 X + H~ b_1 - b_2
+    StepArgs a{cur, oth, scr.xs, oth, 1.0, 1.0, (K == 1) ? 0.0 : -1.0, lpr, cq};
     PF_CHECK(launch_ham_step(plan, kind, a, s));
     PF_CHECK(tm.stop());
     PF_CHECK(check_timeout(plan, s));
@@ -1966,7 +2192,7 @@ int filter_batched(std::vector<BatchFilterItem>& items, int kind, int abi_kind, 
       }
       PF_CHECK(slice_in(kind, abi_kind, it.in, g.dim, it.n_b, col0, ncols, W, xs, ba, bb, it.coef[it.K], flag, s));
       BatchJob J{};
-      J.t = StepTables{p.tab.rec, p.tab.grec, tb, tb + ((size_t)1 << g.b) * cs,
+      J.t = StepTables{p.tab.rec, p.tab.rec8, p.tab.grec, tb, tb + ((size_t)1 << g.b) * cs,
                        tb + (((size_t)1 << g.b) + ((size_t)1 << g.nh)) * cs, p.tab.order};
       J.coef = (const double*)(base + Lo.coef_off) + coef_idx;
       J.xs = xs;
@@ -2217,6 +2443,7 @@ static int static_filter(const polfed_model* model, double e_lo, double e_hi, co
                oFlo = carve(nlo * 8), oFhi = carve(nhi * 8), oCx = carve(ncx * 8),
                oRec = carve(nlo * (size_t)g.rec_stride * 2), oGrp = carve((size_t)g.n_groups * sizeof(GroupRec)),
                oErr = carve(64), oCls = carve(34 * 4), oTyp = carve((nlo + nhi + ncx + (size_t)g.n_groups) * es_c),
+               oRec8 = carve(nlo * (size_t)g.rec_stride),
                oScr = carve(filter_scratch_bytes(plan, dtype, lpr));
   if (bytes > kStaticScratchBytes)
     return fail(POLFED_ENOMEM, "polfed_cheb_filter_static needs " + std::to_string(bytes) +
@@ -2236,6 +2463,7 @@ static int static_filter(const polfed_model* model, double e_lo, double e_hi, co
   plan.tab.C_x = (double*)(d + oCx);
   plan.tab.rec = (uint16_t*)(d + oRec);
   plan.tab.grec = (GroupRec*)(d + oGrp);
+  plan.tab.rec8 = (uint8_t*)(d + oRec8);
   plan.err_flag = (int*)(d + oErr);
   // group schedule: class start offsets (host arithmetic on fixed arrays only)
   int32_t cls_start[34] = {0};
@@ -2264,6 +2492,7 @@ static int static_filter(const polfed_model* model, double e_lo, double e_hi, co
   PF_CUDA(cudaMemsetAsync(plan.err_flag, 0, 64, s));
   k_tables_lo<<<(unsigned)((nlo + 255) / 256), 256, 0, s>>>(g, plan.tab.T_lo, plan.tab.U_lo, plan.tab.F_lo);
   k_tables_rec<<<(unsigned)((nlo + 255) / 256), 256, 0, s>>>(g, plan.tab.T_lo, plan.tab.rec);
+  k_tables_rec8<<<(unsigned)((nlo + 255) / 256), 256, 0, s>>>(g, plan.tab.rec, plan.tab.rec8);
   k_tables_hi<<<(unsigned)((nhi + 255) / 256), 256, 0, s>>>(g, plan.tab.T_hi, plan.tab.F_hi);
   k_tables_cx<<<(unsigned)((ncx + 255) / 256), 256, 0, s>>>(g, plan.tab.C_x);
   k_static_order<<<(unsigned)((nhi + 255) / 256), 256, 0, s>>>(g, d_cls, plan.tab.order);

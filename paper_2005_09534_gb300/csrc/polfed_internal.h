@@ -110,6 +110,11 @@ struct HamTables {
   //   last entries (from the end): local index, in the neighbouring popcount
   //   class, of s_lo with the low site of cross bond k flipped
   uint16_t* rec;
+  // [2^b * rec_stride] bytes: the same records with one-byte entries (local
+  // indices are < 256), for the shared-memory copy of the bulk-copy kernel:
+  //   bytes 0-1: s_lo; byte 2: n1; byte 3: n2; bytes 4..: active low-bond
+  //   neighbours (class 1 first); last bytes (from the end): cross neighbours
+  uint8_t* rec8;
   // [n_groups] per-group constants in schedule order (see GroupRec)
   struct GroupRec* grec;
 };
@@ -125,6 +130,19 @@ struct alignas(16) GroupRec {
 
 int build_geometry(const polfed_model* m, int b_override, HamGeometry* g);
 
+// A captured run of Clenshaw step launches (see filter_block).
+struct StepGraph {
+  int kind = 0, K = 0, lpr = 0;
+  double invD = 0.0, lo = 0.0, hi = 0.0;
+  uint64_t coef_hash = 0;
+  uint32_t wait_cap = 0;
+  const void *xs = nullptr, *ba = nullptr, *bb = nullptr;
+  cudaGraphExec_t exec = nullptr;  // null: key seen once, not captured yet
+  int64_t launches = 0;             // step launches of one replay
+  double alg_bytes = 0.0;           // their algorithmic bytes
+  int uses = 0;
+};
+
 class HamPlan {
  public:
   HamGeometry geo;
@@ -138,6 +156,7 @@ class HamPlan {
   double typed_lo[3] = {0, 0, 0}, typed_hi[3] = {0, 0, 0};
   cudaStream_t stream = nullptr;
   bool stream_alloc = false;  // tables from cudaMallocAsync
+  std::vector<StepGraph> graphs;  // captured Clenshaw runs on this plan's tables (destroyed with it)
 
   int init(const polfed_model* m, cudaStream_t s, bool stream_ordered, int b_override = -1);
   int prepare_typed(int kind, double e_lo, double e_hi);  // alpha/beta-scaled tables
@@ -154,6 +173,7 @@ struct StepArgs {
   void* out;
   double cX, cH, cB;
   int lpr;         // lanes per row: slice = 16 * lpr bytes
+  const float* cxcol = nullptr;  // F32 only: per-column cX (device, W floats) in place of cX
 };
 
 // Launch one step (kind = POLFED_F32 / F64 / DF64 storage type).
@@ -174,6 +194,12 @@ struct FilterScratch {
 };
 int filter_block(HamPlan& plan, int kind, const double* coeffs, int K, double invD, const void* in, void* out,
                  int n_b, int abi_kind, FilterScratch& scr, cudaStream_t s, int lpr_hint = 0);
+// FP32 filter with its own coefficients per column: out[:, j] = sum_n coef_j[n] T_n(H~) in[:, j].
+// The block is filtered in slices of W = slice_width(POLFED_F32, choose_lpr(POLFED_F32, n_b)) columns;
+// d_coef (device) holds, per slice q, (K + 1) rows of W floats:
+// d_coef[(q (K + 1) + n) W + j - q W] = coefficient of column j at order n.  in/out as filter_block.
+int filter_block_cols(HamPlan& plan, const float* d_coef, int K, const void* in, void* out, int n_b, int abi_kind,
+                      FilterScratch& scr, cudaStream_t s);
 int apply_block(HamPlan& plan, int kind, const void* in, void* out, int n_b, int abi_kind, FilterScratch& scr,
                 cudaStream_t s, int lpr_hint = 0);
 size_t filter_scratch_bytes(const HamPlan& plan, int kind, int lpr);

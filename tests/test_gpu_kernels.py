@@ -181,3 +181,33 @@ def test_filter_properties_full_size():
     rows = I.sample_rows(dim, 30, 8)
     want = O.h_apply_rows(m.L, m.J1, m.J2, m.Delta, m.h, True, O.basis(L), X.cpu().numpy(), rows, lo, hi)
     assert np.abs(Y1.cpu().numpy()[rows] - want).max() < 1e-12 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("L,n_b", [(12, 16), (12, 7), (18, 64)])
+def test_cheb_filter_per_column_coefficients(L, n_b):
+    """polfed_cheb_filter_cols: every column through its own Chebyshev series
+    (FP32), against the oracle's matrix three-term recurrence column by column;
+    L = 12 runs the generic step kernel, L = 18 with 64 columns the TMA kernel."""
+    torch, dev = torch_dev()
+    pf = lib()
+    import scipy.sparse as sp
+    dim, st = device_basis(pf, torch, dev, L)
+    m = models(L)[0]
+    H, _ = O.sparse_hamiltonian(m.L, m.J1, m.J2, m.Delta, m.h, m.periodic)
+    b = 1.01 * (m.L * 0.75 + 0.5 * float(np.abs(m.h).sum()))
+    Ht = sp.csr_matrix(H / b)
+    K = 40
+    rng = np.random.default_rng(L + n_b)
+    C = rng.standard_normal((n_b, K + 1)) / np.sqrt(np.arange(1, K + 2))
+    X = I.block(dim, n_b, 77)
+    want = np.stack([O.filter_matrix_powers(Ht, X[:, [j]], C[j], 1.0)[:, 0] for j in range(n_b)], axis=1)
+    Xd = torch.from_numpy(X).to(dev, torch.float32)
+    Yd = torch.empty_like(Xd)
+    pf.cheb_filter_cols(m, st, dim, -b, b, C, Xd, Yd, n_b)
+    err = np.abs(Yd.double().cpu().numpy() - want).max() / (np.abs(X).max() * np.abs(C).sum(axis=1).max())
+    assert err < 2e-7 * (K + 1) + 1e-6, err
+    # one column's own series equals the scalar-coefficient filter of that column
+    j = n_b // 2
+    Y1 = torch.empty_like(Xd)
+    pf.cheb_filter(m, st, dim, -b, b, 0.0, K, Xd, Y1, n_b, pf.F32, coeffs=C[j])
+    assert torch.allclose(Yd[:, j], Y1[:, j], rtol=0, atol=1e-5 * float(np.abs(C[j]).sum() * np.abs(X).max()))
