@@ -617,13 +617,14 @@ def run_filter_only(args, pf, torch, dev):
     Y = torch.empty_like(X)
     b = field_free_bound(m)
     reps = max(1, args.reps)
+    stream = torch.cuda.Stream(device=dev)  # a capturable stream (the Clenshaw loop may run as a CUDA graph)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     c0 = pf.get_counters()
     torch.cuda.synchronize()
-    ev0.record()
+    ev0.record(stream)
     for _ in range(reps):
-        pf.cheb_filter(m, st, dim, -b, b, 0.0, args.K, X, Y, n_b, kind)
-    ev1.record()
+        pf.cheb_filter(m, st, dim, -b, b, 0.0, args.K, X, Y, n_b, kind, stream=stream)
+    ev1.record(stream)
     torch.cuda.synchronize()
     c1 = pf.get_counters()
     k = {pf.F64: 0, pf.F32: 1, pf.DF64: 2}[kind]

@@ -355,6 +355,18 @@ struct NF32 {
     if (hb) r = fmaf(k.cB, b2v, r);
     return r;
   }
+  // the same combination in two parts: e = cX x + cB b2 when x and b2 arrive,
+  // then cH (d x1 + o1 a1 + o2 a2) + e
+  static __device__ __forceinline__ S pre(S xv, S b2v, const KC& k, bool hx, bool hb, C cx) {
+    float e = hx ? cx * xv : 0.f;
+    if (hb) e = fmaf(k.cB, b2v, e);
+    return e;
+  }
+  static __device__ __forceinline__ S fin(S x1, A a1, A a2, C ad, const KC& k, bool j2, S e) {
+    float y = ad * x1 + k.o1 * a1;
+    if (j2) y = fmaf(k.o2, a2, y);
+    return fmaf(k.cH, y, e);
+  }
   static __device__ __forceinline__ float mag(S v) { return fabsf(v); }
 };
 
@@ -374,6 +386,16 @@ struct NF64 {
     if (hx) r = fma(cx, xv, r);
     if (hb) r = fma(k.cB, b2v, r);
     return r;
+  }
+  static __device__ __forceinline__ S pre(S xv, S b2v, const KC& k, bool hx, bool hb, C cx) {
+    double e = hx ? cx * xv : 0.0;
+    if (hb) e = fma(k.cB, b2v, e);
+    return e;
+  }
+  static __device__ __forceinline__ S fin(S x1, A a1, A a2, C ad, const KC& k, bool j2, S e) {
+    double y = ad * x1 + k.o1 * a1;
+    if (j2) y = fma(k.o2, a2, y);
+    return fma(k.cH, y, e);
   }
   static __device__ __forceinline__ float mag(S v) { return (float)fabs(v); }
 };
@@ -404,6 +426,23 @@ struct NDF {
     if (hx) r = df_add(r, df_mul(cx, xv));
     if (hb) r = df_add(r, df_mul(k.cB, b2v));
     return r;
+  }
+  static __device__ __forceinline__ S pre(S xv, S b2v, const KC& k, bool hx, bool hb, C cx) {
+    float2 e = make_float2(0.f, 0.f);
+    if (k.exact) {
+      if (hx) e = make_float2(cx.x * xv.x, cx.x * xv.y);
+      if (hb) e = df_add(e, make_float2(k.cB.x * b2v.x, k.cB.x * b2v.y));
+      return e;
+    }
+    if (hx) e = df_mul(cx, xv);
+    if (hb) e = df_add(e, df_mul(k.cB, b2v));
+    return e;
+  }
+  static __device__ __forceinline__ S fin(S x1, A a1, A a2, C ad, const KC& k, bool j2, S e) {
+    float2 y = df_add(df_mul(ad, x1), df_mul(k.o1, fast_two_sum(a1.x, a1.y)));
+    if (j2) y = df_add(y, df_mul(k.o2, fast_two_sum(a2.x, a2.y)));
+    const float2 r = k.exact ? make_float2(k.cH.x * y.x, k.cH.x * y.y) : df_mul(k.cH, y);
+    return df_add(r, e);
   }
   static __device__ __forceinline__ float mag(S v) { return fabsf(v.x); }
 };
@@ -924,9 +963,14 @@ struct TmaShape {
   static constexpr int UNITS = 32 * CW / LPR;
   static constexpr int RPT = (252 + UNITS - 1) / UNITS;
 };
-using TmaShapeA = TmaShape<16, 4>;  // 544 threads, 2 rows of 2 chunks per lane
-using TmaShapeB = TmaShape<24, 8>;  // 800 threads, 3 rows of 1 chunk per lane
+// 544 threads, 2 rows of 2 chunks per lane.  Measured on GB300 (L = 22 XXZ and
+// L = 20 J1-J2 slices, FP32 and float-float): 24 consumer warps with one chunk
+// per lane (800 threads) and 16 warps with four chunks per lane (one row each)
+// were 4-25% slower.
+using TmaShapeA = TmaShape<16, 4>;
 __host__ __device__ constexpr int tma_stages(bool j2) { return j2 ? 3 : 4; }
+// int4 words of GroupRec::hn_base the producer reads: up to 16 (XXZ) or 28 (J1-J2) high neighbours
+__host__ __device__ constexpr int tma_high_words(bool j2) { return j2 ? 7 : 4; }
 
 template <class NT, bool J2, class SH>
 __global__ void __launch_bounds__(SH::THREADS, 1)
@@ -992,12 +1036,49 @@ __global__ void __launch_bounds__(SH::THREADS, 1)
   if (warp == 0) {
     // ------------------------------------------------------------ producer
     if (lane32 == 0) {
-      int q = 0;      // ring items issued
-      int n_own = 0;  // own tiles issued
+      // The producer is one thread and its issue rate bounds the kernel: the
+      // group's fields come in a few vector loads (the next record is
+      // prefetched into L1 a group ahead), the item loops are unrolled over
+      // the static bond counts, and ring slots and phases are tracked with
+      // counters instead of divisions.
+      int q = 0;        // ring items issued
+      int slot = 0;     // q % NS
+      uint32_t ph = 0;  // bit s: parity of the next empty-phase wait on slot s
+      int n_own = 0;    // own tiles issued
       bool ok = true;
+      constexpr int HN4 = tma_high_words(J2);  // int4 words of hn_base read
+      auto issue = [&](const S* src, int rows) -> bool {
+        if (q >= NS) {
+          const uint32_t par = (ph >> slot) & 1u;
+          if (!mbar_try_wait(&empty[slot], par) && !mbar_wait(&empty[slot], par, &s_abort, wait_cap)) return false;
+          ph ^= 1u << slot;
+        }
+        const uint32_t bytes = (uint32_t)rows * (uint32_t)(W * esz);
+        mbar_expect_tx(&full[slot], bytes);
+        bulk_load(ring + (size_t)slot * stg, src, bytes, &full[slot]);
+        q++;
+        slot = (slot + 1 == NS) ? 0 : slot + 1;
+        return true;
+      };
       for (int ord = 0; ord < n_my && ok; ord++) {
         const GroupRec* G = t.grec + (int)blockIdx.x + ord * (int)gridDim.x;
-        const int r0 = G->r0, n_g = G->n_g;
+        if (ord + 1 < n_my) {
+          const char* nx = reinterpret_cast<const char*>(G + gridDim.x);
+          asm volatile("prefetch.global.L1 [%0];" ::"l"(nx));
+          asm volatile("prefetch.global.L1 [%0];" ::"l"(nx + 128));
+        }
+        const int4* G4 = reinterpret_cast<const int4*>(G);
+        const int4 w0 = __ldg(G4), w1 = __ldg(G4 + 1);
+        int4 hw[HN4];
+#pragma unroll
+        for (int j = 0; j < HN4; j++) hw[j] = __ldg(G4 + 2 + j);
+        const int4 cb0 = __ldg(G4 + 10), cn0 = __ldg(G4 + 12);
+        int4 cb1 = make_int4(0, 0, 0, 0), cn1 = make_int4(0, 0, 0, 0);
+        if constexpr (J2) {
+          cb1 = __ldg(G4 + 11);
+          cn1 = __ldg(G4 + 13);
+        }
+        const int r0 = w0.x, n_g = w0.y, n_hn = w1.x;
         if (ord >= 2 && !mbar_wait(&own_empty[ord & 1], (uint32_t)(((ord >> 1) - 1) & 1), &s_abort, wait_cap)) {
           ok = false;
           break;
@@ -1009,39 +1090,29 @@ __global__ void __launch_bounds__(SH::THREADS, 1)
           bulk_load(own + (size_t)(ord & 1) * stg, b1 + (size_t)r0 * W, bytes, &own_full[ord & 1]);
           n_own++;
         }
-        // items: cross blocks, high blocks, x, b2
-        const int n_items = MAXCR + G->n_hn + 2;
-        for (int it = 0; it < n_items && ok; it++) {
-          const S* src = nullptr;
-          int rows = 0;
-          if (it < MAXCR) {
-            if (it < g.n_cross && G->cr_n[it] > 0) {
-              src = b1 + (size_t)G->cr_base[it] * W;
-              rows = G->cr_n[it];
-            }
-          } else if (it < MAXCR + G->n_hn) {
-            src = b1 + (size_t)G->hn_base[it - MAXCR] * W;
-            rows = n_g;
-          } else if (it == MAXCR + G->n_hn) {
-            if (has_x) {
-              src = x + (size_t)r0 * W;
-              rows = n_g;
-            }
-          } else if (has_b2) {
-            src = b2 + (size_t)r0 * W;
-            rows = n_g;
-          }
-          if (!src) continue;
-          const int slot = q % NS;
-          if (q >= NS && !mbar_wait(&empty[slot], (uint32_t)(((q / NS) - 1) & 1), &s_abort, wait_cap)) {
-            ok = false;
-            break;
-          }
-          const uint32_t bytes = (uint32_t)((size_t)rows * W * esz);
-          mbar_expect_tx(&full[slot], bytes);
-          bulk_load(ring + (size_t)slot * stg, src, bytes, &full[slot]);
-          q++;
+        // items: x, b2 (consumed first and released at once), cross blocks, high blocks
+        if (has_x && !issue(x + (size_t)r0 * W, n_g)) {
+          ok = false;
+          break;
         }
+        if (has_b2 && !issue(b2 + (size_t)r0 * W, n_g)) {
+          ok = false;
+          break;
+        }
+        const int cbase[8] = {cb0.x, cb0.y, cb0.z, cb0.w, cb1.x, cb1.y, cb1.z, cb1.w};
+        const int cnum[8] = {cn0.x, cn0.y, cn0.z, cn0.w, cn1.x, cn1.y, cn1.z, cn1.w};
+#pragma unroll
+        for (int k = 0; k < MAXCR; k++)
+          if (ok && k < g.n_cross && cnum[k] > 0 && !issue(b1 + (size_t)cbase[k] * W, cnum[k])) ok = false;
+        if (!ok) break;
+#pragma unroll
+        for (int j = 0; j < HN4; j++) {
+          const int hb[4] = {hw[j].x, hw[j].y, hw[j].z, hw[j].w};
+#pragma unroll
+          for (int u = 0; u < 4; u++)
+            if (ok && 4 * j + u < n_hn && !issue(b1 + (size_t)hb[u] * W, n_g)) ok = false;
+        }
+        if (!ok) break;
       }
       if (!ok) {
         s_abort = 1;
@@ -1087,13 +1158,12 @@ __global__ void __launch_bounds__(SH::THREADS, 1)
     chk[0] = (lane + 4 * (unit & 1)) * VEC;
     chk[1] = (lane + 4 * (1 - (unit & 1))) * VEC;
   } else {
-    chk[0] = lane * VEC;
+    // a lane's NCH chunks are adjacent; their order rotates with the row unit,
+    // so the NCH-row phases of a warp read NCH different bank groups
+#pragma unroll
+    for (int h = 0; h < NCH; h++) chk[h] = (lane * NCH + ((h + unit) % NCH)) * VEC;
   }
-  C cxl[VL];  // cX of the lane's elements (per column, or the step's scalar)
-#pragma unroll
-  for (int h = 0; h < NCH; h++)
-#pragma unroll
-    for (int v = 0; v < VEC; v++) cxl[h * VEC + v] = col_cx<NT>(cxcol, chk[h] + v, kc);
+
   const C* gFhi = reinterpret_cast<const C*>(t.F_hi);
   int cr_lb[MAXCR], cr_c2[MAXCR];
 #pragma unroll
@@ -1121,6 +1191,42 @@ __global__ void __launch_bounds__(SH::THREADS, 1)
     const int r0 = G->r0, n_g = G->n_g, cls_base = G->cls_base;
     const int n_hn = G->n_hn, n_hn1 = G->n_hn1, need = G->need_mask;
     const S* tile = own + (size_t)(ord & 1) * stg;
+    // ---- x and b2 (the group's first ring items): e = cX x + cB b2, then both slots are free
+    S e[RPT][VL];
+    {
+      int x_slot = -1, b2_slot = -1;
+      if (has_x) {
+        x_slot = q % NS;
+        if (!mbar_wait(&full[x_slot], (uint32_t)((q / NS) & 1), &s_abort, wait_cap)) s_abort = 1;
+        q++;
+      }
+      if (has_b2 && !s_abort) {
+        b2_slot = q % NS;
+        if (!mbar_wait(&full[b2_slot], (uint32_t)((q / NS) & 1), &s_abort, wait_cap)) s_abort = 1;
+        q++;
+      }
+      if (s_abort) break;
+#pragma unroll
+      for (int i = 0; i < RPT; i++) {
+        const int row = unit + UNITS * i;
+#pragma unroll
+        for (int h = 0; h < NCH; h++) {
+          V16<S> xv, bv;
+          const size_t lo = (size_t)(row < n_g ? row : 0) * W + chk[h];
+          if (has_x) xv.i = *reinterpret_cast<const int4*>(ring + (size_t)x_slot * stg + lo);
+          if (has_b2) bv.i = *reinterpret_cast<const int4*>(ring + (size_t)b2_slot * stg + lo);
+#pragma unroll
+          for (int v = 0; v < VEC; v++)
+            e[i][h * VEC + v] = NT::pre(has_x ? xv.s[v] : S(), has_b2 ? bv.s[v] : S(), kc, has_x, has_b2,
+                                        col_cx<NT>(cxcol, chk[h] + v, kc));
+        }
+      }
+      __syncwarp();
+      if (lane32 == 0) {
+        if (x_slot >= 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[x_slot])) : "memory");
+        if (b2_slot >= 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[b2_slot])) : "memory");
+      }
+    }
     A a1[RPT][VL], a2[RPT][VL];
 #pragma unroll
     for (int i = 0; i < RPT; i++)
@@ -1180,8 +1286,7 @@ __global__ void __launch_bounds__(SH::THREADS, 1)
       }
 #undef PF_E
     }
-    // ---- ring items in the producer's order: cross blocks, high blocks, x, b2
-    int x_slot = -1, b2_slot = -1;
+    // ---- ring items in the producer's order: cross blocks, high blocks
     for (int k = 0; k < MAXCR; k++) {
       if (!(k < g.n_cross && G->cr_n[k] > 0)) continue;
       const int slot = q % NS;
@@ -1218,17 +1323,6 @@ __global__ void __launch_bounds__(SH::THREADS, 1)
       q++;
     }
     if (s_abort) break;
-    if (has_x) {
-      x_slot = q % NS;
-      if (!mbar_wait(&full[x_slot], (uint32_t)((q / NS) & 1), &s_abort, wait_cap)) s_abort = 1;
-      q++;
-    }
-    if (has_b2 && !s_abort) {
-      b2_slot = q % NS;
-      if (!mbar_wait(&full[b2_slot], (uint32_t)((q / NS) & 1), &s_abort, wait_cap)) s_abort = 1;
-      q++;
-    }
-    if (s_abort) break;
     // ---- diagonal, combination, store
 #pragma unroll
     for (int i = 0; i < RPT; i++) {
@@ -1239,24 +1333,18 @@ __global__ void __launch_bounds__(SH::THREADS, 1)
 #pragma unroll
         for (int h = 0; h < NCH; h++) {
           const size_t lo = (size_t)row * W + chk[h];
-          V16<S> xo, xv, bv, res;
+          V16<S> xo, res;
           xo.i = *reinterpret_cast<const int4*>(tile + lo);
-          if (has_x) xv.i = *reinterpret_cast<const int4*>(ring + (size_t)x_slot * stg + lo);
-          if (has_b2) bv.i = *reinterpret_cast<const int4*>(ring + (size_t)b2_slot * stg + lo);
 #pragma unroll
           for (int v = 0; v < VEC; v++)
-            res.s[v] = NT::combine(has_x ? xv.s[v] : S(), xo.s[v], has_b2 ? bv.s[v] : S(), a1[i][h * VEC + v],
-                                   a2[i][h * VEC + v], ad, kc, has_x, has_b2, J2, cxl[h * VEC + v]);
+            res.s[v] = NT::fin(xo.s[v], a1[i][h * VEC + v], a2[i][h * VEC + v], ad, kc, J2, e[i][h * VEC + v]);
           __stcg(reinterpret_cast<int4*>(out + (size_t)(r0 + row) * W + chk[h]), res.i);
         }
       }
     }
     __syncwarp();
-    if (lane32 == 0) {
-      if (x_slot >= 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[x_slot])) : "memory");
-      if (b2_slot >= 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[b2_slot])) : "memory");
+    if (lane32 == 0)
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&own_empty[ord & 1])) : "memory");
-    }
   }
   if (s_abort && ctid == 0) atomicExch(err, 1);
 }
@@ -1639,15 +1727,6 @@ static size_t tma_smem_bytes(const HamGeometry& g, size_t esz_c, bool j2) {
          (((size_t)1 << g.b) + ((size_t)1 << g.n_cross)) * esz_c;
 }
 
-// Thread shape of the TMA step kernel: 0 = TmaShapeA, 1 = TmaShapeB (POLFED_TMA_SHAPE).
-static int tma_shape() {
-  static const int v = [] {
-    const char* e = getenv("POLFED_TMA_SHAPE");
-    return e ? atoi(e) : 0;
-  }();
-  return v;
-}
-
 static bool tma_disabled() {
   static const bool v = [] {
     const char* e = getenv("POLFED_NO_TMA");
@@ -1720,11 +1799,10 @@ template <class NT>
 static int launch_step_n(const HamPlan& p, const StepArgs& a, cudaStream_t s) {
   const bool j2 = p.geo.n_low2 + p.geo.n_high2 > 0 || p.geo.J2 != 0.0;
   if (a.lpr == 8 && !tma_disabled() && p.geo.max_group <= 252 &&
+      p.geo.n_high1 + p.geo.n_high2 <= 4 * tma_high_words(j2) &&
       4 + p.geo.n_low1 + p.geo.n_low2 + (j2 ? 6 : 2) <= p.geo.rec_stride &&
       tma_smem_bytes(p.geo, sizeof(typename NT::C), j2) <= 220 * 1024 && p.geo.max_group >= 32 &&
       p.geo.rec_stride == (j2 ? 32 : 16)) {
-    if (tma_shape() == 1)
-      return j2 ? launch_step_tma<NT, true, TmaShapeB>(p, a, s) : launch_step_tma<NT, false, TmaShapeB>(p, a, s);
     return j2 ? launch_step_tma<NT, true, TmaShapeA>(p, a, s) : launch_step_tma<NT, false, TmaShapeA>(p, a, s);
   }
   switch (a.lpr) {
@@ -1925,7 +2003,9 @@ static bool graphs_disabled() {
 // credited per replay.
 static int clenshaw_graph(HamPlan& plan, int kind, const double* c, int K, double invD, FilterScratch& scr, int lpr,
                           cudaStream_t s, void** res) {
-  if (K < 16 || graphs_disabled()) return clenshaw_steps(plan, kind, c, K, invD, scr, lpr, s, res);
+  // the legacy default stream cannot be captured (and the per-thread one is left alone too)
+  if (K < 16 || graphs_disabled() || s == nullptr || s == cudaStreamLegacy || s == cudaStreamPerThread)
+    return clenshaw_steps(plan, kind, c, K, invD, scr, lpr, s, res);
   StepGraph key;
   key.kind = kind;
   key.K = K;
@@ -1939,6 +2019,9 @@ static int clenshaw_graph(HamPlan& plan, int kind, const double* c, int K, doubl
   key.ba = scr.ba;
   key.bb = scr.bb;
   StepGraph* hit = nullptr;
+  for (StepGraph& gr : plan.graphs)
+    if (gr.kind == key.kind && gr.K == key.K && gr.uses < 0 && gr.xs == key.xs && gr.coef_hash == key.coef_hash)
+      return clenshaw_steps(plan, kind, c, K, invD, scr, lpr, s, res);  // capture failed before: stay eager
   for (StepGraph& gr : plan.graphs)
     if (gr.kind == key.kind && gr.K == key.K && gr.lpr == key.lpr && gr.invD == key.invD && gr.lo == key.lo &&
         gr.hi == key.hi && gr.coef_hash == key.coef_hash && gr.wait_cap == key.wait_cap && gr.xs == key.xs &&
@@ -1959,7 +2042,11 @@ static int clenshaw_graph(HamPlan& plan, int kind, const double* c, int K, doubl
     const int64_t l0 = cn.launches, n0 = cn.all_launches[kind];
     const double b0 = cn.all_alg_bytes[kind];
     cudaGraph_t graph = nullptr;
-    PF_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+      cudaGetLastError();  // not capturable here (e.g. the stream is already being captured): run eagerly
+      hit->uses = -1;
+      return clenshaw_steps(plan, kind, c, K, invD, scr, lpr, s, res);
+    }
     void* r = nullptr;
     const int rc = clenshaw_steps(plan, kind, c, K, invD, scr, lpr, s, &r);
     const cudaError_t ec = cudaStreamEndCapture(s, &graph);

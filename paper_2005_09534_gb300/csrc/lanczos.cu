@@ -206,6 +206,7 @@ struct LanczosParams {
   bool fill_panels;    // top the converged set up to whole panels (input of the refinement)
   FilterHook* hook = nullptr;  // batched runner: filter calls go through it
   double guard_dp = 0.02;      // Ritz vectors with theta >= p - guard_dp enter the Rayleigh-Ritz step
+                               // (wider guards, tried for strict refinement targets, made the sweeps stall)
 };
 
 // Y_q = invD sum_n coef[n] T_n(H~) X_q for the panels q (dim x S each), directly
@@ -1210,9 +1211,6 @@ int eigs_impl(polfed_ctx* c, const polfed_model* model, double eps_target, int32
   LanczosParams P{e_lo, e_hi, sigma, K, S, N_ev, o, o.tol_resid * hnorm0 / (0.5 * (e_hi - e_lo)), mixed, false};
   P.hook = hook;
   if (mixed) P.o.tol_conv = std::max(o.tol_conv, 2e-5);  // FP32 filter: stop at its noise floor
-  // a refinement target below tol_resid keeps more guard vectors (theta >= p - 0.07): the pairs at
-  // the window's edge then converge faster from sweep to sweep
-  if (mixed && o.tol_refine > 0.0 && o.tol_refine < o.tol_resid) P.guard_dp = 0.07;
   LanczosOut lo;
   int rc = POLFED_OK, restarts = 0, fallback = 0;
   for (;;) {

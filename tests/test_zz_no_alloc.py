@@ -14,14 +14,24 @@ from gpu_common import device_basis, lib, torch_dev
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("L,n_b,K", [(14, 16, 120), (18, 64, 300)])
-def test_static_filter_matches_allocating_filter_on_two_calls(L, n_b, K):
+def _bound(m):
+    """A bound on ||H|| of Eq. (1): each bond term is at most |J| (1/2 + |Delta|/4), each field |h_i|/2."""
+    nb = m.L if m.periodic else m.L - 1
+    return 1.01 * (nb * (abs(m.J1) + abs(m.J2)) * (0.5 + abs(m.Delta) / 4) + 0.5 * float(np.abs(m.h).sum()))
+
+
+@pytest.mark.parametrize("L,n_b,K,model", [(14, 16, 120, "xxz"), (18, 64, 300, "xxz"), (16, 32, 200, "j1j2"),
+                                             (18, 64, 150, "j1j2")])
+def test_static_filter_matches_allocating_filter_on_two_calls(L, n_b, K, model):
     torch, dev = torch_dev()
     pf = lib()
     dim, st = device_basis(pf, torch, dev, L)
-    m = I.xxz(L, 3.0, 9, 0)
-    lo, hi = -20.0, 19.0
-    for dtype, tdt, tol in ((pf.DF64, torch.float64, 1e-12), (pf.F32, torch.float32, 1e-5)):
+    # the J1-J2 chain (J2 = 1, Delta = 0.55) runs the next-nearest-neighbour tables and kernels
+    m = I.xxz(L, 3.0, 9, 0) if model == "xxz" else I.j1j2(L, 4.0, 9, 1)
+    hi = _bound(m)
+    lo = -hi
+    for dtype, tdt, tol in ((pf.DF64, torch.float64, 1e-12), (pf.F64, torch.float64, 1e-12),
+                            (pf.F32, torch.float32, 1e-5)):
         X = torch.from_numpy(I.block(dim, n_b, L + K)).to(dev, tdt)
         Y_ref = torch.empty_like(X)
         pf.cheb_filter(m, st, dim, lo, hi, 0.0, K, X, Y_ref, n_b, dtype)
@@ -44,3 +54,19 @@ def test_static_filter_rejects_sizes_beyond_the_array():
         pf.cheb_filter_static(I.xxz(L, 3.0, 9, 0), st, dim, -30.0, 30.0, 0.0, 10, X, Y, 64, pf.DF64)
     assert e.value.code == pf.POLFED_ENOMEM
     assert "32" in str(e.value) or "bytes" in str(e.value)
+
+
+def test_static_filter_clears_the_previous_error():
+    """A successful call leaves no stale message from an earlier failure."""
+    torch, dev = torch_dev()
+    pf = lib()
+    L = 12
+    dim, st = device_basis(pf, torch, dev, L)
+    m = I.xxz(L, 2.0, 9, 2)
+    X = torch.from_numpy(I.block(dim, 8, 3)).to(dev)
+    Y = torch.empty_like(X)
+    with pytest.raises(pf.PolfedError):
+        pf.cheb_filter_static(m, st, dim, 1.0, -1.0, 0.0, 10, X, Y, 8, pf.DF64)  # e_lo > e_hi
+    assert pf.last_error() != ""
+    pf.cheb_filter_static(m, st, dim, -_bound(m), _bound(m), 0.0, 10, X, Y, 8, pf.DF64)
+    assert pf.last_error() == ""
