@@ -73,7 +73,8 @@ typedef struct polfed_opts {
   double tol_resid;      /* acceptance: ||H u - E u|| <= tol_resid * ||H||, ||H|| = max(|E_min|, |E_max|) */
   double cols_factor;    /* Lanczos column budget = cols_factor * (1 + k_margin) * N_ev (paper: 2.8) */
   int32_t precision;     /* filter arithmetic: POLFED_F64, POLFED_DF64, or POLFED_F32 for the Lanczos stage
-                            followed by float-float refinement sweeps (Jackson-damped filter + Rayleigh-Ritz) */
+                            followed by refinement sweeps by defect correction (per-column FP32 filters of the
+                            residuals against the Jackson-damped transform, FP64 Rayleigh-Ritz) */
   int32_t bounds_steps;  /* max single-vector Lanczos steps for E_min / E_max */
   int32_t verbose;       /* 1 = progress lines on stderr */
   int32_t dos_rule;      /* how K gets the density of states at the target: POLFED_DOS_* */

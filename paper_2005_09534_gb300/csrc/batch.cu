@@ -76,6 +76,9 @@ class Rendezvous : public FilterHook {
     }
   }
   int plan_b(int L) override { return batch_b(L); }
+  // a realization in its refinement sweeps launches on its own stream: the others' filters need not wait for it
+  void suspend() override { leave(); }
+  void resume() override { enter(); }
 
   void enter() {
     std::unique_lock<std::mutex> lk(mu_);

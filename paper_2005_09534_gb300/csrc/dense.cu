@@ -261,6 +261,44 @@ __global__ void k_panels_to_colmajor(const double* __restrict__ P, int64_t dim, 
   }
 }
 
+// Compact column gather on panel-major blocks (N x S panels): column j of
+// out (j < nc_pad) is column idx[j] of in for j < nc, zero for j >= nc.
+__global__ void k_gather_panel_cols(const double* __restrict__ in, int64_t dim, int S, const int* __restrict__ idx,
+                                    int nc, int nc_pad, double* __restrict__ out) {
+  const int64_t tot = dim * nc_pad;
+  const int64_t pst = dim * S;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = e / pst, rem = e - p * pst;
+    const int64_t r = rem / S;
+    const int c = (int)(rem - r * S);
+    const int j = (int)(p * S + c);
+    double v = 0.0;
+    if (j < nc) {
+      const int src = idx[j];
+      v = in[(int64_t)(src / S) * pst + r * S + (src % S)];
+    }
+    out[e] = v;
+  }
+}
+
+// F_i <- pl_i F_i + G_{pos_i} for every column i of npan panels (pos_i < 0: no
+// G term); G is a compact panel-major block.
+__global__ void k_scale_add_cols(double* F, const double* __restrict__ G, const int* __restrict__ pos,
+                                 const double* __restrict__ pl, int64_t dim, int S, int npan) {
+  const int64_t pst = dim * S;
+  const int64_t tot = pst * npan;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = e / pst, rem = e - p * pst;
+    const int64_t r = rem / S;
+    const int c = (int)(rem - r * S);
+    const int i = (int)(p * S + c);
+    double v = pl[i] * F[e];
+    const int j = pos[i];
+    if (j >= 0) v += G[(int64_t)(j / S) * pst + r * S + (j % S)];
+    F[e] = v;
+  }
+}
+
 // ------------------------------------------------------------------- host
 static int grid_for(int64_t n, int per = 256) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + per - 1) / per, 152 * 8)); }
 
@@ -391,6 +429,22 @@ int Dense::resid(const double* U, double* W, const double* lam_dev, cudaStream_t
 
 int Dense::panels_to_colmajor(const double* P, int n, double* out, cudaStream_t s) {
   k_panels_to_colmajor<<<grid_for(dim * n), 256, 0, s>>>(P, dim, S, n, out);
+  PF_CUDA(cudaGetLastError());
+  count_launch();
+  return POLFED_OK;
+}
+
+int Dense::gather_cols(const double* in, const int* idx_dev, int nc, int nc_pad, double* out, cudaStream_t s) {
+  if (nc_pad <= 0) return POLFED_OK;
+  k_gather_panel_cols<<<grid_for(dim * nc_pad), 256, 0, s>>>(in, dim, S, idx_dev, nc, nc_pad, out);
+  PF_CUDA(cudaGetLastError());
+  count_launch();
+  return POLFED_OK;
+}
+
+int Dense::scale_add_cols(double* F, const double* G, const int* pos_dev, const double* pl_dev, int npan,
+                          cudaStream_t s) {
+  k_scale_add_cols<<<grid_for(dim * S * npan), 256, 0, s>>>(F, G, pos_dev, pl_dev, dim, S, npan);
   PF_CUDA(cudaGetLastError());
   count_launch();
   return POLFED_OK;

@@ -31,6 +31,10 @@ struct Dense {
   int axpbypcz(int64_t n, double a, const double* x, double b, double* y, double c, const double* z, cudaStream_t s);
   int resid(const double* U, double* W, const double* lam_dev, cudaStream_t s);
   int panels_to_colmajor(const double* P, int n, double* out, cudaStream_t s);
+  // out (nc_pad / S panels) = columns idx[0..nc) of the panel-major block in, zero padded
+  int gather_cols(const double* in, const int* idx_dev, int nc, int nc_pad, double* out, cudaStream_t s);
+  // F_i = pl_i F_i + G_{pos_i} (pos_i >= 0) or pl_i F_i (pos_i < 0), npan panels of F, G compact
+  int scale_add_cols(double* F, const double* G, const int* pos_dev, const double* pl_dev, int npan, cudaStream_t s);
   int ensure(void*& p, size_t& have, size_t need);
   void release();
   ~Dense() { release(); }

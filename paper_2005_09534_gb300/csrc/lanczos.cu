@@ -670,65 +670,24 @@ int finish_sweep(polfed_ctx* c, HamPlan& plan, const LanczosParams& P, double* F
   return rr_select(c, plan, P, U, nr, d_evecs, out);
 }
 
-// One refinement sweep (mixed precision): W = Pj(H~) U with the Jackson-damped
-// order-Kr transform of Eq. (2) in float-float arithmetic, W orthonormalized
-// (block Gram-Schmidt twice + Cholesky QR twice per panel), then rr_select on
-// span(W).  U holds nr orthonormal columns in panels (ritz buffer region 0);
-// the padding columns of the last panel are exactly zero and stay zero through
-// the filter, the Gram-Schmidt and the Cholesky QR.  On return region 0 holds W.
-int refine(polfed_ctx* c, HamPlan& plan, const LanczosParams& P, int Kr, int nr, double* d_evecs, LanczosOut& out) {
-  cudaStream_t s = c->stream;
-  Dense& D = c->dense;
-  const int64_t dim = plan.geo.dim;
-  const int S = P.S;
-  const int64_t pstride = dim * S;
-  const int npan = (nr + S - 1) / S;
-  const int opan = (std::min(nr, P.N_ev) + S - 1) / S;
-  PF_CHECK(ensure_ritz(c, dim, S, nr, P.N_ev));
-  double* U = c->ritz.as<double>();
-  double* F = RitzLayout(U, dim, S, nr, P.N_ev).F;
-  std::vector<double> cf, g;
-  double Dn = 1.0;
-  cheb_coeffs(P.sigma, Kr, cf, Dn);
-  jackson(Kr, g);
-  for (int n = 0; n <= Kr; n++) cf[n] *= g[n] / Dn;
-  PF_CHECK(plan.prepare_typed(POLFED_DF64, P.e_lo, P.e_hi));
-  const int lpr = choose_lpr(POLFED_DF64, S);
-  PF_CHECK(c->fscr.ensure(std::max(c->fscr.n, filter_scratch_bytes(plan, POLFED_DF64, lpr)), &c->ws_total,
-                          c->ws_limit));
-  FilterScratch scr;
-  scr.xs = c->fscr.p;
-  scr.bytes = c->fscr.n;
-  const double t0 = now_s();
-  {
-    std::vector<const double*> ins(npan);
-    std::vector<double*> outs(npan);
-    for (int q = 0; q < npan; q++) {
-      ins[q] = U + (size_t)q * pstride;
-      outs[q] = F + (size_t)q * pstride;
-    }
-    PF_CHECK(run_filter(plan, P, POLFED_DF64, cf.data(), Kr, 1.0, ins.data(), outs.data(), npan, S, scr, s, lpr));
-  }
-  out.matvec_cols += (int64_t)Kr * nr;
-  out.t_filter += now_s() - t0;
-  return finish_sweep(c, plan, P, F, nr, d_evecs, out);
-}
-
 // One refinement sweep by defect correction, with the filter in FP32.  For a
 // unit vector u with Rayleigh value lam and residual r = H~ u - lam u, and any
 // polynomial P, P(H~) u = P(lam) u + g(H~) r with g(x) = (P(x) - P(lam)) /
 // (x - lam), a polynomial of degree Kr - 1.  Only g(H~) r goes through the
 // FP32 Chebyshev filter; since |r| is small (the FP32 stage leaves |r| about
-// 1e-6), its FP32 rounding error is that much smaller than the float-float
-// filter's, and the sweep costs an FP32 filter of the block.  Steps: the
+// 1e-6), its FP32 rounding error is that much smaller than that of an FP32
+// filter of u, and the sweep costs an FP32 filter of the block.  Steps: the
 // Rayleigh-Ritz basis of span(U) with H~ in FP64 (u_i, lam_i, r_i for all nr
 // columns), the Chebyshev coefficients of each column's g by synthetic
 // division (FP64, host), the per-column FP32 filter of the residual block,
-// W = U diag(P(lam)) + g(H~) R, then the same orthonormalization and
-// Rayleigh-Ritz as the float-float sweep.  P is the Jackson-damped order-Kr
-// transform of Eq. (2).
-int refine_dd(polfed_ctx* c, HamPlan& plan, const LanczosParams& P, int Kr, int nr, double* d_evecs,
-              LanczosOut& out) {
+// W = U diag(P(lam)) + g(H~) R, then orthonormalization and Rayleigh-Ritz
+// (finish_sweep).  P is the Jackson-damped order-Kr transform of Eq. (2).
+// Columns whose residual is already at most tol_lock are locked: they skip
+// the filter (W_i = P(lam_i) u_i, the same scale) and stay in the block for
+// the orthonormalization and Rayleigh-Ritz, so a sweep filters only the
+// columns still converging.
+int refine_dd(polfed_ctx* c, HamPlan& plan, const LanczosParams& P, int Kr, int nr, double tol_lock,
+              double* d_evecs, LanczosOut& out, int* n_filtered) {
   cudaStream_t s = c->stream;
   Dense& D = c->dense;
   const int64_t dim = plan.geo.dim;
@@ -766,7 +725,23 @@ int refine_dd(polfed_ctx* c, HamPlan& plan, const LanczosParams& P, int Kr, int 
   PF_CHECK(D.update(R.Wr, pstride, npan, G, 1, nr_pad, nr, R.T, pstride, 1.0, 0.0, s));
   PF_CUDA(cudaMemcpyAsync(lam_d, lam.data(), nr_pad * sizeof(double), cudaMemcpyHostToDevice, s));
   for (int q = 0; q < npan; q++) PF_CHECK(D.resid(R.F + (size_t)q * pstride, R.T + (size_t)q * pstride, lam_d + q * S, s));
-  // 3. coefficients: a_n of the damped transform, and per column the synthetic
+  // 3. residual norms: the columns above the lock threshold are filtered, packed into whole panels
+  std::vector<double> rn(nr_pad, 0.0);
+  for (int q = 0; q < npan; q++)
+    PF_CHECK(D.coldot(R.T + (size_t)q * pstride, R.T + (size_t)q * pstride, S, rn.data() + (size_t)q * S, s));
+  std::vector<int> idx, pos(nr_pad, -1);
+  for (int i = 0; i < nr; i++)
+    if (!(std::sqrt(std::max(0.0, rn[i])) <= tol_lock)) {
+      pos[i] = (int)idx.size();
+      idx.push_back(i);
+    }
+  const int nc = (int)idx.size();
+  const int npc = (nc + S - 1) / S;
+  *n_filtered = nc;
+  if (debug_on())
+    fprintf(stderr, "[polfed] defect-correction sweep (Kr %d): %d of %d columns filtered, %d locked\n", Kr, nc, nr,
+            nr - nc);
+  // 4. coefficients: a_n of the damped transform, and per filtered column the synthetic
   //    division g = (P - P(lam)) / (x - lam) in the Chebyshev basis, from the top:
   //    d_{Kr-1} = 2 a_Kr, d_{n-1} = 2 (a_n + lam d_n) - d_{n+1} (n >= 2), d_0 = a_1 + lam d_1 - d_2 / 2
   //    (x T_0 = T_1, x T_m = (T_{m+1} + T_{m-1}) / 2)
@@ -775,11 +750,11 @@ int refine_dd(polfed_ctx* c, HamPlan& plan, const LanczosParams& P, int Kr, int 
   cheb_coeffs(P.sigma, Kr, a, Dn);
   jackson(Kr, gj);
   for (int n = 0; n <= Kr; n++) a[n] *= gj[n] / Dn;
-  const int Kg = Kr - 1;                         // degree of g
+  const int Kg = Kr - 1;                                                // degree of g
   const int W32 = slice_width(POLFED_F32, choose_lpr(POLFED_F32, S));  // columns per FP32 slice
-  const int nsl = (S + W32 - 1) / W32;           // slices per panel
+  const int nsl = (S + W32 - 1) / W32;                                  // slices per panel
   const size_t per_panel = (size_t)nsl * (Kg + 1) * W32;
-  std::vector<float> coef((size_t)npan * per_panel, 0.f);
+  std::vector<float> coef((size_t)npc * per_panel, 0.f);
   std::vector<double> pl(nr_pad, 0.0), d(Kr + 2);
   for (int i = 0; i < nr; i++) {
     const double l = lam[i];
@@ -791,36 +766,44 @@ int refine_dd(polfed_ctx* c, HamPlan& plan, const LanczosParams& P, int Kr, int 
       b1 = b0;
     }
     pl[i] = a[0] + l * b1 - b2;
+    if (pos[i] < 0) continue;
     std::fill(d.begin(), d.end(), 0.0);
     d[Kr - 1] = 2.0 * a[Kr];
     for (int n = Kr - 1; n >= 2; n--) d[n - 1] = 2.0 * (a[n] + l * d[n]) - d[n + 1];
     if (Kr >= 2) d[0] = a[1] + l * d[1] - 0.5 * d[2];
-    const int q = i / S, col = i % S, sl = col / W32, j = col % W32;
+    const int j = pos[i], q = j / S, col = j % S, sl = col / W32, jj = col % W32;
     float* base = coef.data() + (size_t)q * per_panel + (size_t)sl * (Kg + 1) * W32;
-    for (int n = 0; n <= Kg; n++) base[(size_t)n * W32 + j] = (float)d[n];
+    for (int n = 0; n <= Kg; n++) base[(size_t)n * W32 + jj] = (float)d[n];
   }
-  PF_CHECK(c->coefbuf.ensure(coef.size() * sizeof(float) + 256, &c->ws_total, c->ws_limit));
+  const size_t coef_bytes = (coef.size() * sizeof(float) + 255) & ~(size_t)255;
+  PF_CHECK(c->coefbuf.ensure(coef_bytes + ((size_t)nr_pad + nc + 64) * sizeof(int), &c->ws_total, c->ws_limit));
   float* coef_d = c->coefbuf.as<float>();
-  PF_CUDA(cudaMemcpyAsync(coef_d, coef.data(), coef.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+  int* pos_d = reinterpret_cast<int*>(reinterpret_cast<char*>(coef_d) + coef_bytes);
+  int* idx_d = pos_d + nr_pad;
+  if (!coef.empty())
+    PF_CUDA(cudaMemcpyAsync(coef_d, coef.data(), coef.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+  PF_CUDA(cudaMemcpyAsync(pos_d, pos.data(), (size_t)nr_pad * sizeof(int), cudaMemcpyHostToDevice, s));
+  if (nc > 0) PF_CUDA(cudaMemcpyAsync(idx_d, idx.data(), (size_t)nc * sizeof(int), cudaMemcpyHostToDevice, s));
+  PF_CUDA(cudaMemcpyAsync(lam_d, pl.data(), nr_pad * sizeof(double), cudaMemcpyHostToDevice, s));
   const double t1 = now_s();
   out.t_ritz += t1 - t0;
-  // 4. Wr = g(H~) T per column, FP32
-  PF_CHECK(plan.prepare_typed(POLFED_F32, P.e_lo, P.e_hi));
-  const int lpr32 = choose_lpr(POLFED_F32, S);
-  PF_CHECK(c->fscr.ensure(std::max(c->fscr.n, filter_scratch_bytes(plan, POLFED_F32, lpr32)), &c->ws_total,
-                          c->ws_limit));
-  FilterScratch scr;
-  scr.xs = c->fscr.p;
-  scr.bytes = c->fscr.n;
-  for (int q = 0; q < npan; q++)
-    PF_CHECK(filter_block_cols(plan, coef_d + (size_t)q * per_panel, Kg, R.T + (size_t)q * pstride,
-                               R.Wr + (size_t)q * pstride, S, POLFED_F64, scr, s));
-  out.matvec_cols += (int64_t)Kg * nr;
-  // 5. Wr += F diag(P(lam)): the filtered block
-  for (int i = 0; i < nr_pad; i++) pl[i] = -pl[i];
-  PF_CUDA(cudaMemcpyAsync(lam_d, pl.data(), nr_pad * sizeof(double), cudaMemcpyHostToDevice, s));
-  for (int q = 0; q < npan; q++) PF_CHECK(D.resid(R.F + (size_t)q * pstride, R.Wr + (size_t)q * pstride, lam_d + q * S, s));
-  PF_CUDA(cudaMemcpyAsync(R.F, R.Wr, (size_t)npan * pstride * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  // 5. Wr = the filtered columns of T, packed; T = g(H~) Wr per column, FP32
+  if (nc > 0) {
+    PF_CHECK(D.gather_cols(R.T, idx_d, nc, npc * S, R.Wr, s));
+    PF_CHECK(plan.prepare_typed(POLFED_F32, P.e_lo, P.e_hi));
+    const int lpr32 = choose_lpr(POLFED_F32, S);
+    PF_CHECK(c->fscr.ensure(std::max(c->fscr.n, filter_scratch_bytes(plan, POLFED_F32, lpr32)), &c->ws_total,
+                            c->ws_limit));
+    FilterScratch scr;
+    scr.xs = c->fscr.p;
+    scr.bytes = c->fscr.n;
+    for (int q = 0; q < npc; q++)
+      PF_CHECK(filter_block_cols(plan, coef_d + (size_t)q * per_panel, Kg, R.Wr + (size_t)q * pstride,
+                                 R.T + (size_t)q * pstride, S, POLFED_F64, scr, s));
+    out.matvec_cols += (int64_t)Kg * nc;
+  }
+  // 6. F_i = P(lam_i) u_i + g_i(H~) r_i (locked columns: P(lam_i) u_i), the filtered block
+  PF_CHECK(D.scale_add_cols(R.F, R.T, pos_d, lam_d, npan, s));
   PF_CUDA(cudaStreamSynchronize(s));
   out.t_filter += now_s() - t1;
   return finish_sweep(c, plan, P, R.F, nr, d_evecs, out);
@@ -1244,7 +1227,7 @@ int eigs_impl(polfed_ctx* c, const polfed_model* model, double eps_target, int32
   }
   if (rc != POLFED_OK && rc != POLFED_ENOCONV) return rc;
   if (mixed && lo.n_out > 0) {
-    // refinement sweeps with a float-float filter until the residuals pass
+    // refinement sweeps (defect correction with FP32 filters) until the residuals pass
     int Kr = std::max(16, K / 2);
     if (sigma == 0.0) Kr &= ~1;
     double mr_prev = 1e300;
@@ -1254,20 +1237,35 @@ int eigs_impl(polfed_ctx* c, const polfed_model* model, double eps_target, int32
     // a target below tol_resid (eigenvector-derived observables) allows more sweeps; the
     // wanted pairs near the window's edge gain a roughly constant factor per sweep
     const bool strict = tol_ref_t < P.tol_resid_t;
-    const int max_sweeps = strict ? 40 : 6;
+    // a column whose residual is already half the target skips the next sweep's filter
+    constexpr double kLockFrac = 0.5;
+    const int max_sweeps = strict ? 40 : 24;
+    // a float-float run in place of the sweeps costs about twice the FP32 stage's filter work
+    const double fallback_cost = 2.0 * (double)std::max(lo.m, 1) * S * K;
+    int n_filt = lo.ritz_cols;  // columns the next sweep filters, about
     for (int sweep = 0; sweep < max_sweeps; sweep++) {
       double mr = 0.0;
       for (double r : lo.resid_t) mr = std::max(mr, r);
       if (lo.n_out >= N_ev && mr <= tol_ref_t && sweep > 0) break;
-      if (sweep >= 3 && mr > (strict ? 0.95 : 0.5) * mr_prev) break;  // stagnating: more sweeps will not help
+      if (sweep >= 2 && mr > 0.0 && mr_prev > 0.0) {
+        // from the second sweep on (order K) the worst residual falls by a steady factor per sweep
+        const double r = mr / mr_prev;
+        if (r > 0.95) break;  // stagnating: the block misses part of the wanted subspace
+        // converging too slowly: the sweeps still needed at this rate, each filtering about as many
+        // columns as the last one, would cost more than the float-float run
+        if (!strict && mr > tol_ref_t &&
+            std::log(tol_ref_t / mr) / std::log(r) * (double)n_filt * Kr > fallback_cost)
+          break;
+      }
       mr_prev = mr;
       if (o.verbose || debug_on())
         fprintf(stderr, "[polfed] refinement sweep %d: Kr %d, max resid (H~) before %.3e\n", sweep + 1, Kr, mr);
       const double tr0 = now_s();
-      // the batched runner's filter rendezvous takes one coefficient set per block: it keeps the
-      // float-float sweep; the direct path corrects the defect with the FP32 filter
-      const int rrc = hook ? refine(c, plan, P, Kr, lo.ritz_cols, d_evecs, lo)
-                           : refine_dd(c, plan, P, Kr, lo.ritz_cols, d_evecs, lo);
+      // the sweep's per-column filters launch on the context's own stream: a batched runner's
+      // rendezvous stops waiting for this realization meanwhile
+      if (hook) hook->suspend();
+      const int rrc = refine_dd(c, plan, P, Kr, lo.ritz_cols, kLockFrac * tol_ref_t, d_evecs, lo, &n_filt);
+      if (hook) hook->resume();
       lo.t_ritz += now_s() - tr0;
       if (rrc != POLFED_OK) return rrc;
       notify(c, POLFED_PHASE_REFINE, sweep);

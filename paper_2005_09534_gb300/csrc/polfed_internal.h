@@ -233,6 +233,9 @@ struct FilterHook {
   virtual int filter(HamPlan& plan, int kind, const double* coef, int K, double invD, const double* const* in,
                      double* const* out, int npan, int S, cudaStream_t s) = 0;
   virtual int plan_b(int L) { return -1; }  // low/high split for the plans (-1 = default)
+  // the caller launches its own kernels until resume() and sends no filter() meanwhile
+  virtual void suspend() {}
+  virtual void resume() {}
   virtual ~FilterHook() {}
 };
 // Context internals for the other translation units.
