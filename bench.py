@@ -653,7 +653,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="L22_xxz_W3", choices=sorted(WORKLOADS) + sorted(BATCHED))
     ap.add_argument("--precision", default=None, choices=sorted(PREC),
-                    help="filter arithmetic (default: f32 stage + refinement; df64 for batched workloads)")
+                    help="filter arithmetic (default: f32 stage + refinement)")
     ap.add_argument("--dos", default="mlp", choices=sorted(DOS),
                     help="density-of-states rule for K (mlp: the learned predictor, trained before timing)")
     ap.add_argument("--batch-mode", default="batched", choices=["batched", "sequential"],
@@ -664,7 +664,7 @@ def main():
     ap.add_argument("--reps", type=int, default=1, help="--filter-only: filter calls")
     args = ap.parse_args()
     if args.precision is None:
-        args.precision = "df64" if args.workload in BATCHED else "f32"
+        args.precision = "f32"
     if args.warmup < 3 and not args.filter_only:
         print("warning: fewer than 3 warm-up steps; the number is not valid", file=sys.stderr)
     if args.impl == "reference":
