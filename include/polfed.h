@@ -85,8 +85,8 @@ typedef struct polfed_opts {
                             Lanczos probe confirms that they contain the spectrum, else ignored (0, 0 = none) */
   int32_t kpm_moments;   /* POLFED_DOS_KPM: Chebyshev moments (default 256) */
   int32_t kpm_vectors;   /* POLFED_DOS_KPM: random vectors of the stochastic trace (default 16) */
-  double tol_refine;     /* POLFED_F32: refinement sweeps continue (at most 6) until every residual is
-                            <= tol_refine * ||H||; 0 = tol_resid.  Eigenvector-derived quantities such as the
+  double tol_refine;     /* POLFED_F32: refinement sweeps continue (at most 24; 40 when tol_refine < tol_resid)
+                            until every residual is <= tol_refine * ||H||; 0 = tol_resid.  Eigenvector-derived quantities such as the
                             entanglement entropy move with the eigenvector error ~ residual / level spacing, so
                             a smaller value buys them accuracy; acceptance still uses tol_resid */
 } polfed_opts;
@@ -322,8 +322,10 @@ int polfed_block_lanczos(polfed_ctx* ctx, const polfed_model* model, double e_lo
  * With K = 0, a run that finds fewer than N_ev Ritz values with P >= p (the
  * density of states was overestimated) restarts, at most twice, with a
  * smaller K.  With precision POLFED_F32 the FP32-stage pairs are refined by
- * up to four float-float filter + Rayleigh-Ritz sweeps; if they stall short
- * of tol_resid, a float-float (POLFED_DF64) run replaces the result.
+ * defect-correction sweeps (FP32 per-column filters of the residuals, FP64
+ * Rayleigh-Ritz; columns already at half the target are locked); if the
+ * sweeps stagnate, or would cost more than a float-float run at their
+ * observed rate, a float-float (POLFED_DF64) run replaces the result.
  * Blocking.  Returns POLFED_ENOCONV with partial results if the column
  * budget ran out. */
 int polfed_eigs(polfed_ctx* ctx, const polfed_model* model, double eps_target, int32_t N_ev, int32_t K, int32_t n_b,
