@@ -1,4 +1,5 @@
-// FP64 dense block operations of block Lanczos (Eqs. (3)-(4)):
+// Dense block operations of block Lanczos (Eqs. (3)-(4)), FP64 in and out
+// (the two contractions compute in float-float, see below):
 //   Gram:   C_j = Q_j^T R for a set of N x S panels (re-orthogonalization, A_j, Rayleigh-Ritz)
 //   update: Out = beta Out + alpha sum_j Q_j C_j (re-orthogonalization, Ritz vectors u_i = Q t_i)
 //   Cholesky QR of an N x S panel (Q_{j+1} B_{j+1} = R_{j+1}), random start block,
@@ -12,8 +13,42 @@
 
 namespace polfed {
 
+// ------------------------------------------------- float-float arithmetic
+// GB300 runs FP64 FMAs at about 1/58 of its FP32 rate, and its FP64 tensor
+// path is no faster, so the block contractions below compute in float-float
+// on the FP32 pipes: an FP64 operand x is split into hi = fl32(x) and
+// lo = fl32(x - hi) (x = hi + lo to about 2^-48 relative), a product is
+// hi*hi with its exact rounding error (an FMA) plus the two cross terms, and
+// a sum is kept as an unevaluated pair (h, l) grown by Knuth's two-sum and
+// renormalized by Dekker's fast two-sum after every tile of rows.  The lo*lo
+// term (2^-48 relative) is dropped.  Results go back to FP64 as h + l.
+__device__ __forceinline__ float2 ff_split(double v) {
+  const float h = __double2float_rn(v);
+  return make_float2(h, __double2float_rn(__dsub_rn(v, (double)h)));
+}
+// (h, l) += x * y
+// (the _rn intrinsics keep the compiler from contracting these into FMAs,
+// which would break the error terms)
+__device__ __forceinline__ void ff_fma(float& h, float& l, float2 x, float2 y) {
+  const float p = __fmul_rn(x.x, y.x);
+  float e = fmaf(x.x, y.x, -p);
+  e = fmaf(x.x, y.y, e);
+  e = fmaf(x.y, y.x, e);
+  const float s = __fadd_rn(h, p);
+  const float bv = __fsub_rn(s, h);
+  const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bv)), __fsub_rn(p, bv));
+  h = s;
+  l = __fadd_rn(l, __fadd_rn(err, e));
+}
+__device__ __forceinline__ void ff_norm(float& h, float& l) {
+  const float s = __fadd_rn(h, l);
+  l = __fsub_rn(l, __fsub_rn(s, h));
+  h = s;
+}
+
 // ------------------------------------------------------------------ Gram
 // partial[(chunk * J + j) * S * S + a * S + b] = sum_{rows in chunk} Q_j[r][a] R[r][b]
+// (float-float accumulation over the chunk, FP64 partials)
 template <int S>
 __global__ void __launch_bounds__(256) k_gram(const double* __restrict__ Q, int64_t pstride,
                                                const double* __restrict__ R, int64_t dim, int64_t rows_per_chunk,
@@ -21,28 +56,28 @@ __global__ void __launch_bounds__(256) k_gram(const double* __restrict__ Q, int6
   constexpr int T = S / 16;  // thread tile T x T
   constexpr int RT = S >= 128 ? 16 : 32;
   extern __shared__ __align__(16) double sh[];
-  double* sQ = sh;           // RT x S
-  double* sR = sh + RT * S;  // RT x S
+  float2* sQ = reinterpret_cast<float2*>(sh);  // RT x S (hi, lo)
+  float2* sR = sQ + RT * S;                    // RT x S
   const int j = blockIdx.y;
   const int64_t r0 = (int64_t)blockIdx.x * rows_per_chunk;
   const int64_t r1 = min(dim, r0 + rows_per_chunk);
   const double* Qj = Q + (int64_t)j * pstride;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  double acc[T][T];
+  float ah[T][T], al[T][T];
 #pragma unroll
   for (int a = 0; a < T; a++)
 #pragma unroll
-    for (int b = 0; b < T; b++) acc[a][b] = 0.0;
+    for (int b = 0; b < T; b++) ah[a][b] = al[a][b] = 0.f;
   for (int64_t rb = r0; rb < r1; rb += RT) {
     const int nr = (int)min((int64_t)RT, r1 - rb);
     for (int e = threadIdx.x; e < RT * S; e += 256) {
       const int rr = e / S;
-      sQ[e] = rr < nr ? Qj[(rb + rr) * S + (e - rr * S)] : 0.0;
-      sR[e] = rr < nr ? R[(rb + rr) * S + (e - rr * S)] : 0.0;
+      sQ[e] = ff_split(rr < nr ? Qj[(rb + rr) * S + (e - rr * S)] : 0.0);
+      sR[e] = ff_split(rr < nr ? R[(rb + rr) * S + (e - rr * S)] : 0.0);
     }
     __syncthreads();
     for (int rr = 0; rr < nr; rr++) {
-      double q[T], r[T];
+      float2 q[T], r[T];
 #pragma unroll
       for (int a = 0; a < T; a++) q[a] = sQ[rr * S + ty + 16 * a];
 #pragma unroll
@@ -50,15 +85,19 @@ __global__ void __launch_bounds__(256) k_gram(const double* __restrict__ Q, int6
 #pragma unroll
       for (int a = 0; a < T; a++)
 #pragma unroll
-        for (int b = 0; b < T; b++) acc[a][b] = fma(q[a], r[b], acc[a][b]);
+        for (int b = 0; b < T; b++) ff_fma(ah[a][b], al[a][b], q[a], r[b]);
     }
+#pragma unroll
+    for (int a = 0; a < T; a++)
+#pragma unroll
+      for (int b = 0; b < T; b++) ff_norm(ah[a][b], al[a][b]);
     __syncthreads();
   }
   double* P = partial + ((int64_t)blockIdx.x * J + j) * S * S;
 #pragma unroll
   for (int a = 0; a < T; a++)
 #pragma unroll
-    for (int b = 0; b < T; b++) P[(ty + 16 * a) * S + tx + 16 * b] = acc[a][b];
+    for (int b = 0; b < T; b++) P[(ty + 16 * a) * S + tx + 16 * b] = (double)ah[a][b] + (double)al[a][b];
 }
 
 // C[(j*S + a) * ldc + col0 + b] = sum_chunk partial[chunk][j][a][b]
@@ -86,32 +125,32 @@ __global__ void __launch_bounds__(256) k_update(const double* __restrict__ Q, in
   constexpr int TR = RT / 16;            // rows per thread
   constexpr int TC = S / 16;             // columns per thread
   extern __shared__ __align__(16) double sh[];
-  double* sC = sh;          // S x S
-  double* sQ = sh + S * S;  // RT x S
+  float2* sC = reinterpret_cast<float2*>(sh);  // S x S (hi, lo)
+  float2* sQ = sC + S * S;                     // RT x S
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int col0 = blockIdx.y * S;
   double* O = Out + (int64_t)blockIdx.y * ostride;
   for (int64_t rb = (int64_t)blockIdx.x * RT; rb < dim; rb += (int64_t)gridDim.x * RT) {
     const int nr = (int)min((int64_t)RT, dim - rb);
-    double acc[TR][TC];
+    float ah[TR][TC], al[TR][TC];  // float-float accumulators
 #pragma unroll
     for (int a = 0; a < TR; a++)
 #pragma unroll
-      for (int b = 0; b < TC; b++) acc[a][b] = 0.0;
+      for (int b = 0; b < TC; b++) ah[a][b] = al[a][b] = 0.f;
     for (int j = 0; j < J; j++) {
       __syncthreads();
       for (int e = threadIdx.x; e < S * S; e += 256) {
         const int a = e / S, b = e - a * S;
-        sC[e] = (col0 + b < ncols_valid) ? C[((int64_t)j * S + a) * crs + (int64_t)(col0 + b) * ccs] : 0.0;
+        sC[e] = ff_split((col0 + b < ncols_valid) ? C[((int64_t)j * S + a) * crs + (int64_t)(col0 + b) * ccs] : 0.0);
       }
       const double* Qj = Q + (int64_t)j * pstride;
       for (int e = threadIdx.x; e < RT * S; e += 256) {
         const int rr = e / S;
-        sQ[e] = rr < nr ? Qj[(rb + rr) * S + (e - rr * S)] : 0.0;
+        sQ[e] = ff_split(rr < nr ? Qj[(rb + rr) * S + (e - rr * S)] : 0.0);
       }
       __syncthreads();
       for (int a = 0; a < S; a++) {
-        double q[TR], c[TC];
+        float2 q[TR], c[TC];
 #pragma unroll
         for (int i = 0; i < TR; i++) q[i] = sQ[(ty + 16 * i) * S + a];
 #pragma unroll
@@ -119,8 +158,12 @@ __global__ void __launch_bounds__(256) k_update(const double* __restrict__ Q, in
 #pragma unroll
         for (int i = 0; i < TR; i++)
 #pragma unroll
-          for (int k = 0; k < TC; k++) acc[i][k] = fma(q[i], c[k], acc[i][k]);
+          for (int k = 0; k < TC; k++) ff_fma(ah[i][k], al[i][k], q[i], c[k]);
       }
+#pragma unroll
+      for (int i = 0; i < TR; i++)
+#pragma unroll
+        for (int k = 0; k < TC; k++) ff_norm(ah[i][k], al[i][k]);
     }
 #pragma unroll
     for (int i = 0; i < TR; i++) {
@@ -129,7 +172,8 @@ __global__ void __launch_bounds__(256) k_update(const double* __restrict__ Q, in
 #pragma unroll
         for (int k = 0; k < TC; k++) {
           const int64_t o = (rb + rr) * S + tx + 16 * k;
-          O[o] = (beta == 0.0 ? 0.0 : beta * O[o]) + alpha * acc[i][k];
+          const double v = (double)ah[i][k] + (double)al[i][k];
+          O[o] = (beta == 0.0 ? 0.0 : beta * O[o]) + alpha * v;
         }
       }
     }
