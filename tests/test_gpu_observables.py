@@ -95,7 +95,7 @@ def test_entropy_product_and_dimer_states():
 
 
 def test_observables_of_polfed_eigenpairs_L14():
-    """The spec parity bar on the method's own output: L = 14 XXZ ring,
+    """The 1e-8 observables bar on the method's own output: L = 14 XXZ ring,
     W = 3, N_ev = 50 at eps = 0.5 from the float-float path; the GPU gap ratio
     and the GPU entropies of the GPU eigenvectors are within 1e-8 of the
     oracle's values on the dense-ED eigenpairs."""
